@@ -1,0 +1,245 @@
+/*
+ * adct.h -- C ABI of the GB300 (sm_103a) library for the 14-addition orthogonal
+ * approximate DCT of Bayer & Cintra, "DCT-like Transform for Image Compression
+ * Requires 14 Additions Only" (arXiv 1702.00817).
+ *
+ * What the library computes (notation of the paper):
+ *   T      the 8x8 matrix with entries in {0, +1, -1} (Sec. 2);
+ *   D      diag(1/sqrt8, 1/sqrt2, 1/2, 1/sqrt2, 1/sqrt8, 1/sqrt2, 1/2, 1/sqrt2), so
+ *          D^2 = diag(2^-a_i), a = (3,1,2,1,3,1,2,1), and C^ = D T is orthogonal (Sec. 2);
+ *   fast algorithm  T = P A3 A2 A1: 14 additions per 8-point transform (Sec. 2, Table 1).
+ * The image codec follows the paper's JPEG-style experiment (Sec. 3): every 8x8
+ * block of a uint8 plane goes through the separable 2D transform, then a
+ * quantiser, then the inverse procedure:
+ *   forward      Z = T (X - 128) T^T                       rows, then columns, integers
+ *   quantise     STEP : q = sgn(Z) floor((2|Z| + Q) / (2Q))  (round half away from zero)
+ *                ZONAL: q = Z if zig-zag rank(i,j) < r, else 0   (Sec. 3)
+ *                STEP_ZONAL: STEP, then the ZONAL mask; NONE: q = Z
+ *   dequantise   S_ij = q_ij Q_ij 2^(6 - a_i - a_j)           (D^2 merged into the step, Sec. 2)
+ *   inverse      R = T^T S T                                (T^-1 = T^T D^2, Sec. 2)
+ *   reconstruct  pixel = clamp(floor((R + 32) / 64) + 128, 0, 255)
+ * Every integer result is exact (no rounding other than the two stated above).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named in adct_image and the float tensors are DEVICE memory
+ *     owned by the caller; the library never frees or retains them after a call
+ *     completes on its stream.  The adct_image and adct_quant arrays themselves
+ *     are HOST memory, read during the call only.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL is the legacy
+ *     default stream).  Argument errors are detected on the host before any
+ *     launch and nothing is launched.  CUDA errors return ADCT_ERR_CUDA with the
+ *     CUDA message kept in adct_last_error().
+ *   - A context is not thread-safe: use one per host thread.
+ *   - A context allocates a small device workspace for per-call descriptor
+ *     tables; calls may overlap on different streams (the workspace is a ring of
+ *     slots guarded by events).
+ */
+#ifndef ADCT_H
+#define ADCT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream handle (identical to cudaStream_t). */
+typedef struct CUstream_st* adct_stream_t;
+
+typedef enum {
+  ADCT_OK = 0,
+  ADCT_ERR_INVALID_ARG = 1, /* null pointer, bad count, bad quantiser or launch parameter */
+  ADCT_ERR_SHAPE = 2,       /* width/height not a positive multiple of 8, bad pitch/stride */
+  ADCT_ERR_ALIGN = 3,       /* src/dst/pitch/plane_stride not 8-byte, coef not 16-byte aligned */
+  ADCT_ERR_OOM = 4,         /* workspace allocation failed */
+  ADCT_ERR_CUDA = 5,        /* a CUDA call failed; see adct_last_error */
+  ADCT_ERR_TIMEOUT = 6,     /* a bounded wait gave up */
+  ADCT_ERR_UNSUPPORTED = 7  /* device is not sm_103 / feature not available */
+} adct_status;
+
+/* Quantiser modes (adct_quant.mode). */
+enum { ADCT_Q_NONE = 0, ADCT_Q_STEP = 1, ADCT_Q_ZONAL = 2, ADCT_Q_STEP_ZONAL = 3 };
+
+typedef struct adct_context adct_context;
+
+/*
+ * One image of `channels` planar uint8 planes, each height x width (multiples of
+ * 8, 8..65536), rows `pitch` bytes apart (pitch >= width), planes
+ * `plane_stride` bytes apart (plane_stride >= pitch * height when channels > 1).
+ * src and dst share pitch and plane_stride.
+ *   src   pixels read by the forward transform            (8-byte aligned)
+ *   dst   reconstructed pixels (may equal src)            (8-byte aligned)
+ *   coef  int16 coefficients, block-major:  coef[((c * Hb + by) * Wb + bx) * 64 + i * 8 + j]
+ *         with Hb = height/8, Wb = width/8, (i, j) = (row, column) frequency  (16-byte aligned)
+ * A pointer an entry point does not use may be NULL.
+ * Coefficient range: |Z_ij| <= 128 * 2^(a_i + a_j) <= 8192, so int16 is exact.
+ */
+typedef struct {
+  const uint8_t* src;
+  uint8_t* dst;
+  int16_t* coef;
+  int32_t width;
+  int32_t height;
+  int32_t channels;
+  int32_t reserved; /* must be 0 */
+  int64_t pitch;
+  int64_t plane_stride;
+} adct_image;
+
+/*
+ * Quantiser.  mode: ADCT_Q_*.  Q: step table, row-major (i*8 + j), each entry in
+ * [1, 65535] (used by STEP and STEP_ZONAL, ignored otherwise: Q = 1).
+ * r: number of zig-zag coefficients kept, 0..64 (ZONAL and STEP_ZONAL).
+ */
+typedef struct {
+  int32_t mode;
+  int32_t r;
+  uint16_t Q[64];
+} adct_quant;
+
+/*
+ * Launch shape of the integer kernels.  Zero fields take the defaults.
+ *   threads_per_cta   multiple of 32 in [32, 1024]
+ *   ctas_per_sm       resident CTAs per SM the persistent grid is sized for (1..32)
+ *   blocks_per_thread 1 or 2 8x8 blocks per thread (2 needs 16-byte aligned rows)
+ *   stage_coef        0: each thread stores its coefficients directly;
+ *                     1: coefficients are staged through shared memory and
+ *                        stored by the warp as contiguous 512-byte rows
+ */
+typedef struct {
+  int32_t threads_per_cta;
+  int32_t ctas_per_sm;
+  int32_t blocks_per_thread;
+  int32_t stage_coef;
+} adct_launch;
+
+/* Create a context on CUDA device `device` (checks for compute capability 10.3).
+ * On success *ctx owns a workspace; release it with adct_destroy. */
+adct_status adct_create(adct_context** ctx, int32_t device);
+
+/* Destroy a context after synchronising its workspace events.  NULL is a no-op. */
+void adct_destroy(adct_context* ctx);
+
+/*
+ * Forward 2D transform (Sec. 2 matrix T applied as the 14-addition fast
+ * algorithm T = P A3 A2 A1, rows then columns; Sec. 3 blockwise over 8x8
+ * blocks): coef = Z = T (src - 128) T^T for every block of the n images.
+ * Uses src and coef.  One launch over all planes of all images.
+ */
+adct_status adct_forward(adct_context* ctx, const adct_image* imgs, int32_t n, adct_stream_t stream);
+
+/*
+ * Quantise coefficients in place (Sec. 2 D^2 merged step quantiser, Sec. 3
+ * zig-zag zonal retention): coef <- q(coef).  Uses coef only.  The input must
+ * hold forward coefficients (|Z_ij| <= 8192); larger magnitudes give
+ * unspecified (but memory-safe) results.
+ */
+adct_status adct_quantise(adct_context* ctx, const adct_image* imgs, int32_t n, const adct_quant* quant,
+                          adct_stream_t stream);
+
+/*
+ * Dequantise with D^2 merged (S_ij = q_ij Q_ij 2^(6 - a_i - a_j), Q = 1 for NONE
+ * and ZONAL), invert R = T^T S T with the transposed 14-addition flow graph, and
+ * reconstruct dst = clamp(floor((R + 32) / 64) + 128, 0, 255) (Sec. 2
+ * orthogonality; Sec. 3 "inverse procedure").  Uses coef and dst.
+ */
+adct_status adct_inverse(adct_context* ctx, const adct_image* imgs, int32_t n, const adct_quant* quant,
+                         adct_stream_t stream);
+
+/*
+ * Fused round trip in one pass over HBM: forward, quantise, then (if dst is
+ * non-NULL) dequantise + inverse + reconstruct.  q is written to coef when coef
+ * is non-NULL.  At least one of coef and dst must be non-NULL.  dst may alias
+ * src (each block is read before it is written).  Results equal adct_forward,
+ * adct_quantise, adct_inverse run in sequence, bit for bit.
+ */
+adct_status adct_roundtrip(adct_context* ctx, const adct_image* imgs, int32_t n, const adct_quant* quant,
+                           adct_stream_t stream);
+
+/*
+ * Differentiable float32 variant (Sec. 2 C^ = D T).  x, y: [planes][H][W]
+ * float32 row-major device tensors (H, W multiples of 8, 16-byte aligned).
+ * y = D T x T^T D per 8x8 block, followed, when Qsoft (HOST array of 64
+ * positive floats, row-major i*8+j) is non-NULL, by the soft quantiser
+ * y <- y - (Q/2pi) sin(2pi y / Q).
+ */
+adct_status adct_forward_f32(adct_context* ctx, const float* x, float* y, int64_t planes, int32_t H, int32_t W,
+                             const float* Qsoft, adct_stream_t stream);
+
+/*
+ * Adjoint of adct_forward_f32 with respect to x (hand-written backward):
+ * gx = T^T D (gy * (1 - cos(2pi y / Q))) D T per block, y recomputed from x
+ * (the factor is 1 when Qsoft is NULL).  Same layout rules as the forward.
+ */
+adct_status adct_backward_f32(adct_context* ctx, const float* x, const float* gy, float* gx, int64_t planes,
+                              int32_t H, int32_t W, const float* Qsoft, adct_stream_t stream);
+
+/* Set / read the launch shape used by the integer entry points of ctx. */
+adct_status adct_set_launch(adct_context* ctx, const adct_launch* launch);
+adct_status adct_get_launch(adct_context* ctx, adct_launch* launch);
+
+/*
+ * Round trip through a CUDA graph cached in ctx per batch signature (image
+ * count, sizes, channel counts, quantiser mode, launch shape and which of
+ * coef/dst are used).  The first call with a signature captures
+ * {descriptor upload; kernel}; later calls rewrite the pinned descriptor
+ * staging buffer and replay.  Results are identical to adct_roundtrip.
+ * *replayed (nullable) is set to 1 when a cached graph was replayed.
+ */
+adct_status adct_roundtrip_graph(adct_context* ctx, const adct_image* imgs, int32_t n, const adct_quant* quant,
+                                 adct_stream_t stream, int32_t* replayed);
+
+/*
+ * Autotune the launch shape for this batch: times each candidate (threads per
+ * CTA x CTAs per SM x blocks per thread x coefficient staging) with CUDA events
+ * over `reps` round trips after one warm-up, keeps the fastest in ctx and
+ * writes it to *best, its mean time in microseconds to *best_us (nullable).
+ * Runs synchronously on `stream`; outputs of the batch are overwritten.
+ */
+adct_status adct_autotune(adct_context* ctx, const adct_image* imgs, int32_t n, const adct_quant* quant,
+                          adct_stream_t stream, int32_t reps, adct_launch* best, float* best_us);
+
+/*
+ * End-to-end round trip on HOST buffers: the adct_image pointers (src, dst,
+ * coef) are host memory (pinned memory gives full copy bandwidth).  Images are
+ * processed in chunks of about chunk_bytes of pixels, each chunk copied to the
+ * device, transformed with adct_roundtrip and copied back, with chunks
+ * pipelined over the context's copy/compute streams.  Device staging is owned
+ * by ctx and grows to the largest chunk.  Synchronous: returns when every
+ * output is in host memory.
+ */
+adct_status adct_roundtrip_host(adct_context* ctx, const adct_image* host_imgs, int32_t n, const adct_quant* quant,
+                                int64_t chunk_bytes);
+
+/*
+ * Diagnostic (host-side, no GPU needed): run the library's own 8-point
+ * butterfly -- the same template the kernels instantiate -- on `count`
+ * vectors of 8 int32 in place, forward (X = T x) or inverse (x = T^T X), and
+ * report the number of additions/subtractions one 8-point transform performs
+ * in *adds (nullable).  Table 1 of the paper gives 14.
+ */
+adct_status adct_butterfly_host(int32_t* vec8, int64_t count, int32_t inverse, int32_t* adds);
+
+/*
+ * Kernel timing for benchmarks.  adct_kernel_timing(ctx, 1) makes every
+ * kernel (or captured graph) the context launches from then on be bracketed
+ * by a pair of CUDA events recorded on the launch stream; 0 stops it.
+ * adct_kernel_time waits for those events and returns the summed device time
+ * of the bracketed launches in *total_ms and the number of kernels launched by
+ * the context since the previous query in *launches (both nullable), then
+ * resets the two counters.
+ */
+adct_status adct_kernel_timing(adct_context* ctx, int32_t enable);
+adct_status adct_kernel_time(adct_context* ctx, double* total_ms, int64_t* launches);
+
+/* Human-readable name of a status code (static string). */
+const char* adct_status_string(adct_status status);
+
+/* Last error message recorded in ctx ("" if none).  Valid until the next call on ctx. */
+const char* adct_last_error(adct_context* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADCT_H */

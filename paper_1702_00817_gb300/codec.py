@@ -1,0 +1,241 @@
+"""Python binding of the codec's C ABI for torch tensors (marshalling only).
+
+Every computation happens in libadct.so's CUDA kernels; this module turns
+torch tensors into adct_image / adct_quant structures, passes the current
+CUDA stream, and raises AdctError on a non-OK status.
+
+Tensor conventions (matching include/adct.h):
+  pixels  uint8 [C, H, W] or [H, W], unit stride along W (rows and planes may be pitched)
+  coef    int16 with C * H * W elements, contiguous; block-major [C, H/8, W/8, 8, 8]
+  float   float32 [..., H, W] contiguous
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _native as N
+from ._native import ADCT_Q_NONE, ADCT_Q_STEP, ADCT_Q_STEP_ZONAL, ADCT_Q_ZONAL, AdctError  # noqa: F401
+
+
+def make_quant(mode: int, Q=None, r: int = 64) -> N.adct_quant:
+    """Quantiser descriptor: mode ADCT_Q_*, Q an 8x8 step table (row-major), r kept zig-zag coefficients."""
+    q = N.adct_quant()
+    q.mode = int(mode)
+    q.r = int(r)
+    vals = [1] * 64 if Q is None else [int(v) for v in (Q.reshape(-1).tolist() if hasattr(Q, "reshape") else Q)]
+    if len(vals) != 64:
+        raise ValueError("Q needs 64 entries")
+    for k, v in enumerate(vals):
+        if not 0 <= v <= 65535:
+            raise ValueError("Q entries must fit uint16")
+        q.Q[k] = v
+    return q
+
+
+@dataclass
+class Image:
+    """One image for the codec: any of src/dst (uint8 pixels) and coef (int16)."""
+    src: torch.Tensor | None = None
+    dst: torch.Tensor | None = None
+    coef: torch.Tensor | None = None
+
+
+def _pix_geometry(t: torch.Tensor):
+    if t.dtype != torch.uint8:
+        raise TypeError("pixel tensors must be uint8")
+    if t.dim() == 2:
+        H, W = t.shape
+        if t.stride(1) != 1:
+            raise ValueError("pixel rows need unit stride")
+        return 1, H, W, t.stride(0), t.stride(0) * H
+    if t.dim() == 3:
+        C, H, W = t.shape
+        if t.stride(2) != 1:
+            raise ValueError("pixel rows need unit stride")
+        return C, H, W, t.stride(1), t.stride(0)
+    raise ValueError("pixel tensors are [H, W] or [C, H, W]")
+
+
+def image_struct(im) -> N.adct_image:
+    if isinstance(im, (tuple, list)):
+        im = Image(*im)
+    ref = im.src if im.src is not None else im.dst
+    s = N.adct_image()
+    if ref is not None:
+        C, H, W, pitch, pstride = _pix_geometry(ref)
+        if im.src is not None and im.dst is not None:
+            g2 = _pix_geometry(im.dst)
+            if g2 != (C, H, W, pitch, pstride):
+                raise ValueError("src and dst must share shape, pitch and plane stride")
+    elif im.coef is not None:
+        # coefficient-only image: [C, H/8, W/8, 8, 8]
+        if im.coef.dim() != 5:
+            raise ValueError("a coefficient-only image needs coef shaped [C, H/8, W/8, 8, 8]")
+        C, hb, wb = im.coef.shape[:3]
+        H, W, pitch, pstride = hb * 8, wb * 8, wb * 8, hb * 8 * wb * 8
+    else:
+        raise ValueError("image has no tensors")
+    if im.coef is not None:
+        if im.coef.dtype != torch.int16 or not im.coef.is_contiguous() or im.coef.numel() != C * H * W:
+            raise ValueError("coef must be contiguous int16 with C*H*W elements")
+    s.src = im.src.data_ptr() if im.src is not None else None
+    s.dst = im.dst.data_ptr() if im.dst is not None else None
+    s.coef = im.coef.data_ptr() if im.coef is not None else None
+    s.width, s.height, s.channels, s.reserved = W, H, C, 0
+    s.pitch, s.plane_stride = pitch, pstride
+    return s
+
+
+def image_array(images):
+    arr = (N.adct_image * max(1, len(images)))()
+    for k, im in enumerate(images):
+        arr[k] = image_struct(im)
+    return arr
+
+
+def _stream_handle(device: int, stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _f32(t: torch.Tensor, name: str):
+    if t.dtype != torch.float32 or not t.is_contiguous() or t.dim() < 2:
+        raise ValueError(f"{name} must be a contiguous float32 tensor [..., H, W]")
+    H, W = t.shape[-2], t.shape[-1]
+    return t.numel() // (H * W), H, W
+
+
+def _qsoft(Qsoft):
+    if Qsoft is None:
+        return None
+    vals = [float(v) for v in (Qsoft.reshape(-1).tolist() if hasattr(Qsoft, "reshape") else Qsoft)]
+    if len(vals) != 64:
+        raise ValueError("Qsoft needs 64 entries")
+    return (ctypes.c_float * 64)(*vals)
+
+
+class Codec:
+    """A library context bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = N.load()
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        N.check(self.lib.adct_create(ctypes.byref(h), self.device), None, "adct_create")
+        self.ctx = h
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.adct_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- integer codec ------------------------------------------------------
+    def _call(self, name, images, quant=None, stream=None):
+        arr = image_array(images)
+        args = [self.ctx, arr, len(images)]
+        if quant is not None:
+            args.append(ctypes.byref(quant))
+        args.append(_stream_handle(self.device, stream))
+        N.check(getattr(self.lib, name)(*args), self.ctx, name)
+
+    def forward(self, images, stream=None):
+        self._call("adct_forward", images, None, stream)
+
+    def quantise(self, images, quant, stream=None):
+        self._call("adct_quantise", images, quant, stream)
+
+    def inverse(self, images, quant, stream=None):
+        self._call("adct_inverse", images, quant, stream)
+
+    def roundtrip(self, images, quant, stream=None):
+        self._call("adct_roundtrip", images, quant, stream)
+
+    def roundtrip_graph(self, images, quant, stream=None) -> bool:
+        arr = image_array(images)
+        rep = ctypes.c_int32(0)
+        st = self.lib.adct_roundtrip_graph(self.ctx, arr, len(images), ctypes.byref(quant),
+                                           _stream_handle(self.device, stream), ctypes.byref(rep))
+        N.check(st, self.ctx, "adct_roundtrip_graph")
+        return bool(rep.value)
+
+    def set_launch(self, threads_per_cta=0, ctas_per_sm=0, blocks_per_thread=0, stage_coef=0):
+        l = N.adct_launch(threads_per_cta, ctas_per_sm, blocks_per_thread, stage_coef)
+        N.check(self.lib.adct_set_launch(self.ctx, ctypes.byref(l)), self.ctx, "adct_set_launch")
+
+    def get_launch(self) -> dict:
+        l = N.adct_launch()
+        N.check(self.lib.adct_get_launch(self.ctx, ctypes.byref(l)), self.ctx, "adct_get_launch")
+        return {f: getattr(l, f) for f, _ in N.adct_launch._fields_}
+
+    def autotune(self, images, quant, reps: int = 5, stream=None):
+        arr = image_array(images)
+        best = N.adct_launch()
+        us = ctypes.c_float(0)
+        st = self.lib.adct_autotune(self.ctx, arr, len(images), ctypes.byref(quant),
+                                    _stream_handle(self.device, stream), int(reps), ctypes.byref(best),
+                                    ctypes.byref(us))
+        N.check(st, self.ctx, "adct_autotune")
+        return {f: getattr(best, f) for f, _ in N.adct_launch._fields_}, us.value
+
+    def roundtrip_host(self, images, quant, chunk_bytes: int = 64 << 20):
+        """End-to-end round trip on host (ideally pinned) tensors; synchronous."""
+        arr = image_array(images)
+        st = self.lib.adct_roundtrip_host(self.ctx, arr, len(images), ctypes.byref(quant), int(chunk_bytes))
+        N.check(st, self.ctx, "adct_roundtrip_host")
+
+    def kernel_timing(self, enable: bool):
+        N.check(self.lib.adct_kernel_timing(self.ctx, 1 if enable else 0), self.ctx, "adct_kernel_timing")
+
+    def kernel_time(self):
+        """(summed kernel ms, kernels launched) since the previous query."""
+        ms = ctypes.c_double(0)
+        n = ctypes.c_int64(0)
+        N.check(self.lib.adct_kernel_time(self.ctx, ctypes.byref(ms), ctypes.byref(n)), self.ctx, "adct_kernel_time")
+        return ms.value, n.value
+
+    # -- float variant ------------------------------------------------------
+    def forward_f32(self, x: torch.Tensor, Qsoft=None, out: torch.Tensor | None = None, stream=None):
+        planes, H, W = _f32(x, "x")
+        y = torch.empty_like(x) if out is None else out
+        _f32(y, "out")
+        st = self.lib.adct_forward_f32(self.ctx, x.data_ptr(), y.data_ptr(), planes, H, W, _qsoft(Qsoft),
+                                       _stream_handle(self.device, stream))
+        N.check(st, self.ctx, "adct_forward_f32")
+        return y
+
+    def backward_f32(self, x: torch.Tensor, gy: torch.Tensor, Qsoft=None, out: torch.Tensor | None = None,
+                     stream=None):
+        planes, H, W = _f32(x, "x")
+        _f32(gy, "gy")
+        gx = torch.empty_like(x) if out is None else out
+        st = self.lib.adct_backward_f32(self.ctx, x.data_ptr(), gy.data_ptr(), gx.data_ptr(), planes, H, W,
+                                        _qsoft(Qsoft), _stream_handle(self.device, stream))
+        N.check(st, self.ctx, "adct_backward_f32")
+        return gx
+
+
+def butterfly_host(vectors, inverse: bool = False):
+    """Run the library's 8-point butterfly on the host; returns (outputs, adds per transform)."""
+    import numpy as np
+    v = np.ascontiguousarray(np.asarray(vectors, dtype=np.int32).reshape(-1, 8)).copy()
+    adds = ctypes.c_int32(0)
+    lib = N.load()
+    st = lib.adct_butterfly_host(v.ctypes.data, v.shape[0], 1 if inverse else 0, ctypes.byref(adds))
+    N.check(st, None, "adct_butterfly_host")
+    return v, adds.value

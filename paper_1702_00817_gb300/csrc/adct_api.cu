@@ -1,0 +1,821 @@
+// C ABI of the codec (include/adct.h): argument validation, per-call
+// descriptor tables, the workspace ring, the CUDA-graph cache, the
+// autotuner and the host-buffer pipeline.  Kernels live in adct_codec.cu and
+// adct_float.cu; this file only prepares their parameters and launches them.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "adct.h"
+#include "adct_internal.h"
+
+using namespace adct;
+
+namespace {
+
+constexpr int kSlots = 4;       // descriptor workspace ring
+constexpr int kPipeSlots = 3;   // host pipeline stages in flight
+
+struct Slot {
+  void* dev = nullptr;
+  void* host = nullptr;
+  size_t cap = 0;
+  cudaEvent_t done = nullptr;
+  bool pending = false;
+};
+
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  void* dev = nullptr;
+  void* host = nullptr;
+  size_t bytes = 0;
+  cudaEvent_t done = nullptr;
+  bool pending = false;
+};
+
+struct PipeSlot {
+  cudaStream_t stream = nullptr;
+  uint8_t* src = nullptr;
+  uint8_t* dst = nullptr;
+  int16_t* coef = nullptr;
+  size_t pix_cap = 0, coef_cap = 0;
+};
+
+}  // namespace
+
+struct adct_context {
+  int device = 0;
+  int sm_count = 0;
+  LaunchShape shape{256, 2, 1, 0};
+  std::string last_error;
+  Slot slots[kSlots];
+  int next_slot = 0;
+  cudaStream_t capture_stream = nullptr;
+  std::unordered_map<std::string, GraphEntry> graphs;
+  PipeSlot pipe[kPipeSlots];
+  // kernel timing (benchmarks): event pairs around each launch while enabled
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> tev;
+  size_t tev_used = 0;
+  int64_t launches = 0;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+      changed = (cudaSetDevice(dev) == cudaSuccess);
+    }
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+adct_status fail(adct_context* ctx, adct_status st, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  return st;
+}
+
+adct_status cuda_fail(adct_context* ctx, cudaError_t e, const char* where) {
+  return fail(ctx, ADCT_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define ADCT_CUDA(ctx, call)                                  \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);  \
+  } while (0)
+
+// Brackets one launch with timing events when the context's timing is on.
+struct TimedLaunch {
+  adct_context* ctx;
+  cudaStream_t stream;
+  cudaEvent_t stop = nullptr;
+  TimedLaunch(adct_context* c, cudaStream_t s) : ctx(c), stream(s) {
+    ++ctx->launches;
+    if (!ctx->timing) return;
+    if (ctx->tev_used == ctx->tev.size()) {
+      cudaEvent_t a = nullptr, b = nullptr;
+      if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+      }
+      ctx->tev.emplace_back(a, b);
+    }
+    auto& pr = ctx->tev[ctx->tev_used++];
+    cudaEventRecord(pr.first, stream);
+    stop = pr.second;
+  }
+  void done() {
+    if (stop) cudaEventRecord(stop, stream);
+    stop = nullptr;
+  }
+};
+
+// Zig-zag rank of each position (Sec. 3 "standard zigzag sequence"):
+// positions ordered by anti-diagonal s = i + j; within a diagonal, even s runs
+// from the bottom-left up (i descending), odd s from the top-right down.
+void zigzag_rank(int rank[64]) {
+  int order[64];
+  for (int k = 0; k < 64; ++k) order[k] = k;
+  std::sort(order, order + 64, [](int a, int b) {
+    const int ia = a / 8, ja = a % 8, ib = b / 8, jb = b % 8;
+    const int sa = ia + ja, sb = ib + jb;
+    if (sa != sb) return sa < sb;
+    return (sa % 2 == 0) ? (ia > ib) : (ia < ib);
+  });
+  for (int k = 0; k < 64; ++k) rank[order[k]] = k;
+}
+
+bool uses_step(int mode) { return mode == ADCT_Q_STEP || mode == ADCT_Q_STEP_ZONAL; }
+bool uses_zonal(int mode) { return mode == ADCT_Q_ZONAL || mode == ADCT_Q_STEP_ZONAL; }
+
+adct_status build_quant(adct_context* ctx, const adct_quant* q, QuantParams& qp) {
+  if (!q) return fail(ctx, ADCT_ERR_INVALID_ARG, "quant is NULL");
+  if (q->mode < ADCT_Q_NONE || q->mode > ADCT_Q_STEP_ZONAL) return fail(ctx, ADCT_ERR_INVALID_ARG, "bad quant mode");
+  if (uses_zonal(q->mode) && (q->r < 0 || q->r > 64)) return fail(ctx, ADCT_ERR_INVALID_ARG, "r outside 0..64");
+  int rank[64];
+  zigzag_rank(rank);
+  for (int k = 0; k < 64; ++k) {
+    const int i = k / 8, j = k % 8;
+    uint32_t Q = 1;
+    if (uses_step(q->mode)) {
+      Q = q->Q[k];
+      if (Q < 1) return fail(ctx, ADCT_ERR_INVALID_ARG, "Q entry below 1");
+    }
+    if (Q == 1) {
+      qp.magic[k] = 0xFFFFFFFFu;
+      qp.bias[k] = 1u;
+    } else {
+      qp.magic[k] = (uint32_t)(((1ull << 32) + Q - 1) / Q);
+      qp.bias[k] = Q / 2;
+    }
+    qp.w[k] = (int32_t)(Q << (6 - scale_exp(i) - scale_exp(j)));
+    qp.keep[k] = (!uses_zonal(q->mode) || rank[k] < q->r) ? -1 : 0;
+  }
+  return ADCT_OK;
+}
+
+enum Need { NEED_SRC = 1, NEED_DST = 2, NEED_COEF = 4 };
+
+// Validates the images and builds the plane descriptor table.
+adct_status build_planes(adct_context* ctx, const adct_image* imgs, int32_t n, int need, std::vector<PlaneDesc>& planes,
+                         std::vector<int64_t>& starts, bool& pitch16) {
+  if (n < 0) return fail(ctx, ADCT_ERR_INVALID_ARG, "negative image count");
+  if (n > 0 && !imgs) return fail(ctx, ADCT_ERR_INVALID_ARG, "imgs is NULL");
+  planes.clear();
+  starts.clear();
+  pitch16 = true;
+  int64_t total = 0;
+  for (int32_t m = 0; m < n; ++m) {
+    const adct_image& im = imgs[m];
+    const std::string at = " (image " + std::to_string(m) + ")";
+    if (im.width <= 0 || im.height <= 0 || im.width % 8 || im.height % 8 || im.width > 65536 || im.height > 65536)
+      return fail(ctx, ADCT_ERR_SHAPE, "width/height must be positive multiples of 8 up to 65536" + at);
+    if (im.channels < 1 || im.reserved != 0) return fail(ctx, ADCT_ERR_INVALID_ARG, "bad channels/reserved" + at);
+    if (im.pitch < im.width) return fail(ctx, ADCT_ERR_SHAPE, "pitch < width" + at);
+    if (im.channels > 1 && im.plane_stride < im.pitch * im.height)
+      return fail(ctx, ADCT_ERR_SHAPE, "plane_stride < pitch * height" + at);
+    if ((need & NEED_SRC) && !im.src) return fail(ctx, ADCT_ERR_INVALID_ARG, "src is NULL" + at);
+    if ((need & NEED_DST) && !im.dst) return fail(ctx, ADCT_ERR_INVALID_ARG, "dst is NULL" + at);
+    if ((need & NEED_COEF) && !im.coef) return fail(ctx, ADCT_ERR_INVALID_ARG, "coef is NULL" + at);
+    if ((uintptr_t)im.src % 8 || (uintptr_t)im.dst % 8 || im.pitch % 8 ||
+        (im.channels > 1 && im.plane_stride % 8) || (uintptr_t)im.coef % 16)
+      return fail(ctx, ADCT_ERR_ALIGN, "src/dst/pitch/plane_stride need 8-byte, coef 16-byte alignment" + at);
+    if ((uintptr_t)im.src % 16 || (uintptr_t)im.dst % 16 || im.pitch % 16 ||
+        (im.channels > 1 && im.plane_stride % 16) || (im.width / 8) % 2)
+      pitch16 = false;
+    const int32_t wb = im.width / 8, hb = im.height / 8;
+    const int64_t nb = (int64_t)wb * hb;
+    for (int32_t c = 0; c < im.channels; ++c) {
+      PlaneDesc d;
+      d.src = im.src ? im.src + (int64_t)c * im.plane_stride : nullptr;
+      d.dst = im.dst ? im.dst + (int64_t)c * im.plane_stride : nullptr;
+      d.coef = im.coef ? im.coef + (int64_t)c * nb * 64 : nullptr;
+      d.pitch = im.pitch;
+      d.first = total;
+      d.wb = wb;
+      d.hb = hb;
+      planes.push_back(d);
+      starts.push_back(total);
+      total += nb;
+    }
+  }
+  starts.push_back(total);
+  return ADCT_OK;
+}
+
+size_t table_bytes(size_t nplanes) { return nplanes * sizeof(PlaneDesc) + (nplanes + 1) * sizeof(int64_t); }
+
+void fill_table(void* host, const std::vector<PlaneDesc>& planes, const std::vector<int64_t>& starts) {
+  std::memcpy(host, planes.data(), planes.size() * sizeof(PlaneDesc));
+  std::memcpy((char*)host + planes.size() * sizeof(PlaneDesc), starts.data(), starts.size() * sizeof(int64_t));
+}
+
+// Takes the next workspace slot, waiting for the work that last used it.
+adct_status acquire_slot(adct_context* ctx, size_t bytes, Slot** out) {
+  Slot& s = ctx->slots[ctx->next_slot];
+  ctx->next_slot = (ctx->next_slot + 1) % kSlots;
+  if (s.pending) {
+    ADCT_CUDA(ctx, cudaEventSynchronize(s.done));
+    s.pending = false;
+  }
+  if (s.cap < bytes) {
+    size_t cap = std::max<size_t>(bytes, 4096);
+    cap = (cap + 4095) / 4096 * 4096;
+    if (s.dev) cudaFree(s.dev);
+    if (s.host) cudaFreeHost(s.host);
+    s.dev = s.host = nullptr;
+    s.cap = 0;
+    if (cudaMalloc(&s.dev, cap) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, ADCT_ERR_OOM, "workspace cudaMalloc failed");
+    }
+    if (cudaMallocHost(&s.host, cap) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(s.dev);
+      s.dev = nullptr;
+      return fail(ctx, ADCT_ERR_OOM, "workspace cudaMallocHost failed");
+    }
+    s.cap = cap;
+  }
+  *out = &s;
+  return ADCT_OK;
+}
+
+adct_status check_shape(adct_context* ctx, const LaunchShape& sh) {
+  if (sh.threads < 32 || sh.threads > 256 || sh.threads % 32 || sh.ctas_per_sm < 1 || sh.ctas_per_sm > 32 ||
+      sh.blocks_per_thread != 1 || sh.stage_coef != 0)
+    return fail(ctx, ADCT_ERR_UNSUPPORTED, "launch shape not supported");
+  return ADCT_OK;
+}
+
+int kind_for_roundtrip(const adct_image* imgs, int32_t n, bool& ok) {
+  bool any_coef = n > 0 && imgs[0].coef, any_dst = n > 0 && imgs[0].dst;
+  ok = true;
+  for (int32_t m = 0; m < n; ++m)
+    if ((imgs[m].coef != nullptr) != any_coef || (imgs[m].dst != nullptr) != any_dst) ok = false;
+  if (any_coef && any_dst) return K_RT_FULL;
+  if (any_dst) return K_RT_PIX;
+  return K_RT_COEF;
+}
+
+int need_for_kind(int kind) {
+  switch (kind) {
+    case K_FORWARD: return NEED_SRC | NEED_COEF;
+    case K_QUANTISE: return NEED_COEF;
+    case K_INVERSE: return NEED_COEF | NEED_DST;
+    case K_RT_FULL: return NEED_SRC | NEED_COEF | NEED_DST;
+    case K_RT_PIX: return NEED_SRC | NEED_DST;
+    default: return NEED_SRC | NEED_COEF;
+  }
+}
+
+// Validates, uploads the descriptor table through a workspace slot and launches.
+adct_status run_codec(adct_context* ctx, const adct_image* imgs, int32_t n, const adct_quant* quant, int kind,
+                      cudaStream_t stream, const LaunchShape& shape) {
+  if (!ctx) return ADCT_ERR_INVALID_ARG;
+  ctx->last_error.clear();
+  adct_status st = check_shape(ctx, shape);
+  if (st != ADCT_OK) return st;
+  CodecLaunch cl{};
+  cl.kind = kind;
+  cl.qmode = QM_NONE;
+  if (kind != K_FORWARD) {
+    st = build_quant(ctx, quant, cl.qp);
+    if (st != ADCT_OK) return st;
+    cl.qmode = (kind == K_INVERSE) ? QM_NONE : quant->mode;
+  }
+  std::vector<PlaneDesc> planes;
+  std::vector<int64_t> starts;
+  st = build_planes(ctx, imgs, n, need_for_kind(kind), planes, starts, cl.pitch16);
+  if (st != ADCT_OK) return st;
+  cl.total = starts.back();
+  if (cl.total == 0) return ADCT_OK;
+  if (kind == K_QUANTISE && quant->mode == ADCT_Q_NONE) return ADCT_OK;  // identity
+  DeviceGuard guard(ctx->device);
+  Slot* slot = nullptr;
+  const size_t bytes = table_bytes(planes.size());
+  st = acquire_slot(ctx, bytes, &slot);
+  if (st != ADCT_OK) return st;
+  fill_table(slot->host, planes, starts);
+  ADCT_CUDA(ctx, cudaMemcpyAsync(slot->dev, slot->host, bytes, cudaMemcpyHostToDevice, stream));
+  cl.planes = (const PlaneDesc*)slot->dev;
+  cl.starts = (const int64_t*)((char*)slot->dev + planes.size() * sizeof(PlaneDesc));
+  cl.nplanes = (int32_t)planes.size();
+  TimedLaunch tl(ctx, stream);
+  cudaError_t e = launch_codec(cl, shape, ctx->sm_count, stream);
+  tl.done();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "codec kernel launch");
+  ADCT_CUDA(ctx, cudaEventRecord(slot->done, stream));
+  slot->pending = true;
+  return ADCT_OK;
+}
+
+adct_status float_params(adct_context* ctx, const float* Qsoft, FloatParams& fp) {
+  for (int k = 0; k < 64; ++k) {
+    const float Q = Qsoft[k];
+    if (!(Q > 0.0f) || !std::isfinite(Q)) return fail(ctx, ADCT_ERR_INVALID_ARG, "Qsoft entries must be positive");
+    fp.c2pi[k] = (float)((double)Q / (2.0 * M_PI));
+    fp.r2[k] = (float)(2.0 / (double)Q);
+  }
+  return ADCT_OK;
+}
+
+adct_status check_float(adct_context* ctx, const void* a, const void* b, const void* c, int64_t planes, int32_t H,
+                        int32_t W) {
+  if (!ctx) return ADCT_ERR_INVALID_ARG;
+  ctx->last_error.clear();
+  if (planes < 0) return fail(ctx, ADCT_ERR_INVALID_ARG, "negative plane count");
+  if (H <= 0 || W <= 0 || H % 8 || W % 8) return fail(ctx, ADCT_ERR_SHAPE, "H and W must be positive multiples of 8");
+  if (planes > 0 && (!a || !b || !c)) return fail(ctx, ADCT_ERR_INVALID_ARG, "NULL tensor");
+  if ((uintptr_t)a % 16 || (uintptr_t)b % 16 || (uintptr_t)c % 16)
+    return fail(ctx, ADCT_ERR_ALIGN, "float tensors must be 16-byte aligned");
+  return ADCT_OK;
+}
+
+std::string graph_key(const adct_image* imgs, int32_t n, const adct_quant* q, int kind, const LaunchShape& sh) {
+  std::string k;
+  k.reserve(64 + 16 * (size_t)n);
+  auto put = [&k](const void* p, size_t sz) { k.append((const char*)p, sz); };
+  put(&kind, sizeof kind);
+  put(&sh, sizeof sh);
+  put(q, sizeof *q);
+  put(&n, sizeof n);
+  for (int32_t m = 0; m < n; ++m) {
+    const int32_t dims[3] = {imgs[m].width, imgs[m].height, imgs[m].channels};
+    put(dims, sizeof dims);
+  }
+  return k;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* adct_status_string(adct_status s) {
+  switch (s) {
+    case ADCT_OK: return "ADCT_OK";
+    case ADCT_ERR_INVALID_ARG: return "ADCT_ERR_INVALID_ARG";
+    case ADCT_ERR_SHAPE: return "ADCT_ERR_SHAPE";
+    case ADCT_ERR_ALIGN: return "ADCT_ERR_ALIGN";
+    case ADCT_ERR_OOM: return "ADCT_ERR_OOM";
+    case ADCT_ERR_CUDA: return "ADCT_ERR_CUDA";
+    case ADCT_ERR_TIMEOUT: return "ADCT_ERR_TIMEOUT";
+    case ADCT_ERR_UNSUPPORTED: return "ADCT_ERR_UNSUPPORTED";
+  }
+  return "ADCT_ERR_UNKNOWN";
+}
+
+const char* adct_last_error(adct_context* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+adct_status adct_create(adct_context** out, int32_t device) {
+  if (!out) return ADCT_ERR_INVALID_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return ADCT_ERR_INVALID_ARG;
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return ADCT_ERR_CUDA;
+  if (prop.major != 10 || prop.minor != 3) return ADCT_ERR_UNSUPPORTED;  // kernels are built for sm_103a only
+  adct_context* ctx = new adct_context();
+  ctx->device = device;
+  ctx->sm_count = prop.multiProcessorCount;
+  DeviceGuard guard(device);
+  for (auto& s : ctx->slots) {
+    if (cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess) {
+      adct_destroy(ctx);
+      return ADCT_ERR_CUDA;
+    }
+  }
+  if (cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    adct_destroy(ctx);
+    return ADCT_ERR_CUDA;
+  }
+  *out = ctx;
+  return ADCT_OK;
+}
+
+void adct_destroy(adct_context* ctx) {
+  if (!ctx) return;
+  DeviceGuard guard(ctx->device);
+  for (auto& s : ctx->slots) {
+    if (s.done) {
+      if (s.pending) cudaEventSynchronize(s.done);
+      cudaEventDestroy(s.done);
+    }
+    if (s.dev) cudaFree(s.dev);
+    if (s.host) cudaFreeHost(s.host);
+  }
+  for (auto& kv : ctx->graphs) {
+    GraphEntry& g = kv.second;
+    if (g.pending) cudaEventSynchronize(g.done);
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    if (g.done) cudaEventDestroy(g.done);
+    if (g.dev) cudaFree(g.dev);
+    if (g.host) cudaFreeHost(g.host);
+  }
+  for (auto& p : ctx->pipe) {
+    if (p.stream) {
+      cudaStreamSynchronize(p.stream);
+      cudaStreamDestroy(p.stream);
+    }
+    if (p.src) cudaFree(p.src);
+    if (p.dst) cudaFree(p.dst);
+    if (p.coef) cudaFree(p.coef);
+  }
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  for (auto& pr : ctx->tev) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  delete ctx;
+}
+
+adct_status adct_set_launch(adct_context* ctx, const adct_launch* l) {
+  if (!ctx || !l) return ADCT_ERR_INVALID_ARG;
+  LaunchShape sh = ctx->shape;
+  if (l->threads_per_cta) sh.threads = l->threads_per_cta;
+  if (l->ctas_per_sm) sh.ctas_per_sm = l->ctas_per_sm;
+  if (l->blocks_per_thread) sh.blocks_per_thread = l->blocks_per_thread;
+  sh.stage_coef = l->stage_coef;
+  adct_status st = check_shape(ctx, sh);
+  if (st != ADCT_OK) return st;
+  ctx->shape = sh;
+  return ADCT_OK;
+}
+
+adct_status adct_get_launch(adct_context* ctx, adct_launch* l) {
+  if (!ctx || !l) return ADCT_ERR_INVALID_ARG;
+  l->threads_per_cta = ctx->shape.threads;
+  l->ctas_per_sm = ctx->shape.ctas_per_sm;
+  l->blocks_per_thread = ctx->shape.blocks_per_thread;
+  l->stage_coef = ctx->shape.stage_coef;
+  return ADCT_OK;
+}
+
+adct_status adct_kernel_timing(adct_context* ctx, int32_t enable) {
+  if (!ctx) return ADCT_ERR_INVALID_ARG;
+  ctx->timing = enable != 0;
+  return ADCT_OK;
+}
+
+adct_status adct_kernel_time(adct_context* ctx, double* total_ms, int64_t* launches) {
+  if (!ctx) return ADCT_ERR_INVALID_ARG;
+  DeviceGuard guard(ctx->device);
+  double sum = 0.0;
+  for (size_t k = 0; k < ctx->tev_used; ++k) {
+    ADCT_CUDA(ctx, cudaEventSynchronize(ctx->tev[k].second));
+    float ms = 0.f;
+    ADCT_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->tev[k].first, ctx->tev[k].second));
+    sum += ms;
+  }
+  if (total_ms) *total_ms = sum;
+  if (launches) *launches = ctx->launches;
+  ctx->tev_used = 0;
+  ctx->launches = 0;
+  return ADCT_OK;
+}
+
+adct_status adct_forward(adct_context* ctx, const adct_image* imgs, int32_t n, adct_stream_t stream) {
+  return run_codec(ctx, imgs, n, nullptr, K_FORWARD, (cudaStream_t)stream, ctx ? ctx->shape : LaunchShape{});
+}
+
+adct_status adct_quantise(adct_context* ctx, const adct_image* imgs, int32_t n, const adct_quant* quant,
+                          adct_stream_t stream) {
+  return run_codec(ctx, imgs, n, quant, K_QUANTISE, (cudaStream_t)stream, ctx ? ctx->shape : LaunchShape{});
+}
+
+adct_status adct_inverse(adct_context* ctx, const adct_image* imgs, int32_t n, const adct_quant* quant,
+                         adct_stream_t stream) {
+  return run_codec(ctx, imgs, n, quant, K_INVERSE, (cudaStream_t)stream, ctx ? ctx->shape : LaunchShape{});
+}
+
+adct_status adct_roundtrip(adct_context* ctx, const adct_image* imgs, int32_t n, const adct_quant* quant,
+                           adct_stream_t stream) {
+  if (!ctx) return ADCT_ERR_INVALID_ARG;
+  if (n < 0 || (n > 0 && !imgs)) return fail(ctx, ADCT_ERR_INVALID_ARG, "bad image list");
+  bool ok = true;
+  const int kind = kind_for_roundtrip(imgs, n, ok);
+  if (!ok) return fail(ctx, ADCT_ERR_INVALID_ARG, "coef/dst must be set on all images or on none");
+  if (n > 0 && !imgs[0].coef && !imgs[0].dst) return fail(ctx, ADCT_ERR_INVALID_ARG, "need coef or dst");
+  return run_codec(ctx, imgs, n, quant, kind, (cudaStream_t)stream, ctx->shape);
+}
+
+adct_status adct_forward_f32(adct_context* ctx, const float* x, float* y, int64_t planes, int32_t H, int32_t W,
+                             const float* Qsoft, adct_stream_t stream) {
+  adct_status st = check_float(ctx, x, y, y, planes, H, W);
+  if (st != ADCT_OK) return st;
+  FloatParams fp;
+  if (Qsoft && (st = float_params(ctx, Qsoft, fp)) != ADCT_OK) return st;
+  DeviceGuard guard(ctx->device);
+  TimedLaunch tl(ctx, (cudaStream_t)stream);
+  cudaError_t e = launch_float_forward(x, y, planes, H, W, Qsoft ? &fp : nullptr, ctx->sm_count, (cudaStream_t)stream);
+  tl.done();
+  return e == cudaSuccess ? ADCT_OK : cuda_fail(ctx, e, "float forward launch");
+}
+
+adct_status adct_backward_f32(adct_context* ctx, const float* x, const float* gy, float* gx, int64_t planes,
+                              int32_t H, int32_t W, const float* Qsoft, adct_stream_t stream) {
+  adct_status st = check_float(ctx, x, gy, gx, planes, H, W);
+  if (st != ADCT_OK) return st;
+  FloatParams fp;
+  if (Qsoft && (st = float_params(ctx, Qsoft, fp)) != ADCT_OK) return st;
+  DeviceGuard guard(ctx->device);
+  TimedLaunch tl(ctx, (cudaStream_t)stream);
+  cudaError_t e =
+      launch_float_backward(x, gy, gx, planes, H, W, Qsoft ? &fp : nullptr, ctx->sm_count, (cudaStream_t)stream);
+  tl.done();
+  return e == cudaSuccess ? ADCT_OK : cuda_fail(ctx, e, "float backward launch");
+}
+
+adct_status adct_roundtrip_graph(adct_context* ctx, const adct_image* imgs, int32_t n, const adct_quant* quant,
+                                 adct_stream_t stream, int32_t* replayed) {
+  if (!ctx) return ADCT_ERR_INVALID_ARG;
+  ctx->last_error.clear();
+  if (replayed) *replayed = 0;
+  if (n < 0 || (n > 0 && !imgs)) return fail(ctx, ADCT_ERR_INVALID_ARG, "bad image list");
+  bool ok = true;
+  const int kind = kind_for_roundtrip(imgs, n, ok);
+  if (!ok) return fail(ctx, ADCT_ERR_INVALID_ARG, "coef/dst must be set on all images or on none");
+  if (n > 0 && !imgs[0].coef && !imgs[0].dst) return fail(ctx, ADCT_ERR_INVALID_ARG, "need coef or dst");
+  adct_status st = check_shape(ctx, ctx->shape);
+  if (st != ADCT_OK) return st;
+  CodecLaunch cl{};
+  cl.kind = kind;
+  st = build_quant(ctx, quant, cl.qp);
+  if (st != ADCT_OK) return st;
+  cl.qmode = quant->mode;
+  std::vector<PlaneDesc> planes;
+  std::vector<int64_t> starts;
+  st = build_planes(ctx, imgs, n, need_for_kind(kind), planes, starts, cl.pitch16);
+  if (st != ADCT_OK) return st;
+  cl.total = starts.back();
+  if (cl.total == 0) return ADCT_OK;
+  DeviceGuard guard(ctx->device);
+  const std::string key = graph_key(imgs, n, quant, kind, ctx->shape);
+  auto it = ctx->graphs.find(key);
+  const size_t bytes = table_bytes(planes.size());
+  if (it == ctx->graphs.end()) {
+    GraphEntry g;
+    g.bytes = bytes;
+    if (cudaMalloc(&g.dev, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, ADCT_ERR_OOM, "graph workspace cudaMalloc failed");
+    }
+    if (cudaMallocHost(&g.host, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(g.dev);
+      return fail(ctx, ADCT_ERR_OOM, "graph workspace cudaMallocHost failed");
+    }
+    ADCT_CUDA(ctx, cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming));
+    cl.planes = (const PlaneDesc*)g.dev;
+    cl.starts = (const int64_t*)((char*)g.dev + planes.size() * sizeof(PlaneDesc));
+    cl.nplanes = (int32_t)planes.size();
+    cudaStream_t cs = ctx->capture_stream;
+    ADCT_CUDA(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e1 = cudaMemcpyAsync(g.dev, g.host, bytes, cudaMemcpyHostToDevice, cs);
+    cudaError_t e2 = launch_codec(cl, ctx->shape, ctx->sm_count, cs);
+    cudaError_t e3 = cudaStreamEndCapture(cs, &g.graph);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+      cudaGetLastError();
+      if (g.graph) cudaGraphDestroy(g.graph);
+      cudaEventDestroy(g.done);
+      cudaFree(g.dev);
+      cudaFreeHost(g.host);
+      return fail(ctx, ADCT_ERR_CUDA, "graph capture failed");
+    }
+    ADCT_CUDA(ctx, cudaGraphInstantiate(&g.exec, g.graph, 0));
+    it = ctx->graphs.emplace(key, g).first;
+  } else if (replayed) {
+    *replayed = 1;
+  }
+  GraphEntry& g = it->second;
+  if (g.pending) {
+    ADCT_CUDA(ctx, cudaEventSynchronize(g.done));
+    g.pending = false;
+  }
+  fill_table(g.host, planes, starts);
+  TimedLaunch tl(ctx, (cudaStream_t)stream);
+  cudaError_t eg = cudaGraphLaunch(g.exec, (cudaStream_t)stream);
+  tl.done();
+  if (eg != cudaSuccess) return cuda_fail(ctx, eg, "cudaGraphLaunch");
+  ADCT_CUDA(ctx, cudaEventRecord(g.done, (cudaStream_t)stream));
+  g.pending = true;
+  return ADCT_OK;
+}
+
+adct_status adct_autotune(adct_context* ctx, const adct_image* imgs, int32_t n, const adct_quant* quant,
+                          adct_stream_t stream, int32_t reps, adct_launch* best, float* best_us) {
+  if (!ctx || !best || reps < 1) return ADCT_ERR_INVALID_ARG;
+  bool ok = true;
+  if (n < 1 || !imgs) return fail(ctx, ADCT_ERR_INVALID_ARG, "autotune needs at least one image");
+  const int kind = kind_for_roundtrip(imgs, n, ok);
+  if (!ok) return fail(ctx, ADCT_ERR_INVALID_ARG, "coef/dst must be set on all images or on none");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  ADCT_CUDA(ctx, cudaEventCreate(&e0));
+  ADCT_CUDA(ctx, cudaEventCreate(&e1));
+  const int threads_c[] = {64, 128, 256};
+  const int ctas_c[] = {1, 2, 3, 4, 6, 8, 12, 16};
+  float best_t = 1e30f;
+  LaunchShape best_sh = ctx->shape;
+  adct_status result = ADCT_OK;
+  for (int th : threads_c) {
+    for (int cps : ctas_c) {
+      if (th * cps > 2048) continue;
+      LaunchShape sh{th, cps, 1, 0};
+      adct_status st = run_codec(ctx, imgs, n, quant, kind, s, sh);  // warm-up
+      if (st != ADCT_OK) { result = st; goto done; }
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < reps; ++r) {
+        st = run_codec(ctx, imgs, n, quant, kind, s, sh);
+        if (st != ADCT_OK) { result = st; goto done; }
+      }
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { result = cuda_fail(ctx, cudaGetLastError(), "autotune"); goto done; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const float us = 1000.f * ms / reps;
+      if (us < best_t) { best_t = us; best_sh = sh; }
+    }
+  }
+  ctx->shape = best_sh;
+  best->threads_per_cta = best_sh.threads;
+  best->ctas_per_sm = best_sh.ctas_per_sm;
+  best->blocks_per_thread = best_sh.blocks_per_thread;
+  best->stage_coef = best_sh.stage_coef;
+  if (best_us) *best_us = best_t;
+done:
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return result;
+}
+
+adct_status adct_roundtrip_host(adct_context* ctx, const adct_image* himgs, int32_t n, const adct_quant* quant,
+                                int64_t chunk_bytes) {
+  if (!ctx) return ADCT_ERR_INVALID_ARG;
+  ctx->last_error.clear();
+  if (n < 0 || (n > 0 && !himgs)) return fail(ctx, ADCT_ERR_INVALID_ARG, "bad image list");
+  if (chunk_bytes <= 0) chunk_bytes = 64ll << 20;
+  bool ok = true;
+  const int kind = kind_for_roundtrip(himgs, n, ok);
+  if (!ok) return fail(ctx, ADCT_ERR_INVALID_ARG, "coef/dst must be set on all images or on none");
+  if (n == 0) return ADCT_OK;
+  if (!himgs[0].coef && !himgs[0].dst) return fail(ctx, ADCT_ERR_INVALID_ARG, "need coef or dst");
+  // Host-side validation up front (shapes and pointers); device alignment is ours.
+  for (int32_t m = 0; m < n; ++m) {
+    const adct_image& im = himgs[m];
+    if (im.width <= 0 || im.height <= 0 || im.width % 8 || im.height % 8 || im.width > 65536 || im.height > 65536 ||
+        im.channels < 1 || im.pitch < im.width || (im.channels > 1 && im.plane_stride < im.pitch * im.height) ||
+        !im.src)
+      return fail(ctx, ADCT_ERR_SHAPE, "bad host image " + std::to_string(m));
+  }
+  DeviceGuard guard(ctx->device);
+  // chunk boundaries over whole images
+  std::vector<int32_t> bounds{0};
+  int64_t acc = 0;
+  for (int32_t m = 0; m < n; ++m) {
+    const int64_t pix = (int64_t)himgs[m].width * himgs[m].height * himgs[m].channels;
+    if (acc > 0 && acc + pix > chunk_bytes) {
+      bounds.push_back(m);
+      acc = 0;
+    }
+    acc += pix;
+  }
+  bounds.push_back(n);
+  size_t max_pix = 0;
+  for (size_t c = 0; c + 1 < bounds.size(); ++c) {
+    size_t pix = 0;
+    for (int32_t m = bounds[c]; m < bounds[c + 1]; ++m)
+      pix += (size_t)himgs[m].width * himgs[m].height * himgs[m].channels;
+    max_pix = std::max(max_pix, pix);
+  }
+  const bool want_coef = himgs[0].coef != nullptr, want_dst = himgs[0].dst != nullptr;
+  for (auto& p : ctx->pipe) {
+    if (!p.stream) ADCT_CUDA(ctx, cudaStreamCreateWithFlags(&p.stream, cudaStreamNonBlocking));
+    const size_t pix_cap = (max_pix + 255) / 256 * 256;
+    if (p.pix_cap < pix_cap) {
+      cudaStreamSynchronize(p.stream);
+      if (p.src) cudaFree(p.src);
+      if (p.dst) cudaFree(p.dst);
+      p.src = p.dst = nullptr;
+      p.pix_cap = 0;
+      if (cudaMalloc(&p.src, pix_cap) != cudaSuccess || cudaMalloc(&p.dst, pix_cap) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, ADCT_ERR_OOM, "pipeline staging cudaMalloc failed");
+      }
+      p.pix_cap = pix_cap;
+    }
+    if (p.coef_cap < 2 * pix_cap) {
+      cudaStreamSynchronize(p.stream);
+      if (p.coef) cudaFree(p.coef);
+      p.coef = nullptr;
+      p.coef_cap = 0;
+      if (cudaMalloc(&p.coef, 2 * pix_cap) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, ADCT_ERR_OOM, "pipeline staging cudaMalloc failed");
+      }
+      p.coef_cap = 2 * pix_cap;
+    }
+  }
+  std::vector<adct_image> dimgs;
+  for (size_t c = 0; c + 1 < bounds.size(); ++c) {
+    PipeSlot& p = ctx->pipe[c % kPipeSlots];
+    cudaStream_t s = p.stream;
+    dimgs.clear();
+    size_t off = 0;
+    for (int32_t m = bounds[c]; m < bounds[c + 1]; ++m) {
+      const adct_image& h = himgs[m];
+      const size_t plane = (size_t)h.width * h.height;
+      adct_image d{};
+      d.src = p.src + off;
+      d.dst = want_dst ? p.dst + off : nullptr;
+      d.coef = want_coef ? p.coef + off : nullptr;  // 64 int16 per 64 pixels: same element offset
+      d.width = h.width;
+      d.height = h.height;
+      d.channels = h.channels;
+      d.pitch = h.width;
+      d.plane_stride = (int64_t)plane;
+      for (int32_t ch = 0; ch < h.channels; ++ch)
+        ADCT_CUDA(ctx, cudaMemcpy2DAsync(p.src + off + ch * plane, h.width, h.src + (int64_t)ch * h.plane_stride, h.pitch,
+                                         h.width, h.height, cudaMemcpyHostToDevice, s));
+      dimgs.push_back(d);
+      off += plane * h.channels;
+    }
+    adct_status st = run_codec(ctx, dimgs.data(), (int32_t)dimgs.size(), quant, kind, s, ctx->shape);
+    if (st != ADCT_OK) return st;
+    for (size_t k = 0; k < dimgs.size(); ++k) {
+      const adct_image& h = himgs[bounds[c] + (int32_t)k];
+      const adct_image& d = dimgs[k];
+      const size_t plane = (size_t)h.width * h.height;
+      if (want_coef)
+        ADCT_CUDA(ctx, cudaMemcpyAsync(h.coef, d.coef, plane * h.channels * sizeof(int16_t), cudaMemcpyDeviceToHost, s));
+      if (want_dst)
+        for (int32_t ch = 0; ch < h.channels; ++ch)
+          ADCT_CUDA(ctx, cudaMemcpy2DAsync(h.dst + (int64_t)ch * h.plane_stride, h.pitch, d.dst + ch * plane, h.width,
+                                           h.width, h.height, cudaMemcpyDeviceToHost, s));
+    }
+  }
+  for (auto& p : ctx->pipe) ADCT_CUDA(ctx, cudaStreamSynchronize(p.stream));
+  return ADCT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Host-side diagnostic: the kernels' own butterfly templates on a counting type.
+namespace {
+thread_local int64_t g_adds = 0;
+struct Counted {
+  int64_t v;
+};
+inline Counted operator+(Counted a, Counted b) {
+  ++g_adds;
+  return Counted{a.v + b.v};
+}
+inline Counted operator-(Counted a, Counted b) {
+  ++g_adds;
+  return Counted{a.v - b.v};
+}
+}  // namespace
+
+extern "C" adct_status adct_butterfly_host(int32_t* vec8, int64_t count, int32_t inverse, int32_t* adds) {
+  if (count < 0 || (count > 0 && !vec8)) return ADCT_ERR_INVALID_ARG;
+  int64_t per = -1;
+  for (int64_t c = 0; c < count; ++c) {
+    Counted v[8];
+    for (int k = 0; k < 8; ++k) v[k].v = vec8[8 * c + k];
+    g_adds = 0;
+    if (inverse) inv8<1>(v);
+    else fwd8<1>(v);
+    if (per < 0) per = g_adds;
+    if (per != g_adds) return ADCT_ERR_INVALID_ARG;
+    for (int k = 0; k < 8; ++k) vec8[8 * c + k] = (int32_t)v[k].v;
+  }
+  if (adds) {
+    if (per < 0) {
+      Counted v[8] = {};
+      g_adds = 0;
+      if (inverse) inv8<1>(v);
+      else fwd8<1>(v);
+      per = g_adds;
+    }
+    *adds = (int32_t)per;
+  }
+  return ADCT_OK;
+}

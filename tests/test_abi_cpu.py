@@ -1,0 +1,87 @@
+"""CPU checks of the C ABI: the library loads, exports every symbol the header
+declares, and its own butterfly (run on the host through the diagnostic entry
+point) equals the oracle's dense T with exactly 14 additions (Table 1)."""
+import itertools
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1702_00817_gb300 import _build, _native
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return _native.load()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "adct.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(adct_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_binding_exports():
+    assert _declared() == sorted(_native.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    for code, name in [(0, "ADCT_OK"), (2, "ADCT_ERR_SHAPE"), (5, "ADCT_ERR_CUDA"), (7, "ADCT_ERR_UNSUPPORTED")]:
+        assert lib.adct_status_string(code).decode() == name
+
+
+def test_butterfly_equals_dense_T_on_all_ternary_vectors(lib):
+    from paper_1702_00817_gb300.codec import butterfly_host
+    T = oracle.matrix_T()
+    vecs = np.array(list(itertools.product((-1, 0, 1), repeat=8)), np.int32)
+    out, adds = butterfly_host(vecs)
+    assert adds == 14
+    assert np.array_equal(out.astype(np.int64), vecs.astype(np.int64) @ T.T)
+    out_i, adds_i = butterfly_host(vecs, inverse=True)
+    assert adds_i == 14
+    assert np.array_equal(out_i.astype(np.int64), vecs.astype(np.int64) @ T)
+
+
+def test_butterfly_on_unit_and_random_vectors(lib):
+    from paper_1702_00817_gb300.codec import butterfly_host
+    T = oracle.matrix_T()
+    rng = np.random.default_rng(1)
+    vecs = np.concatenate([np.eye(8, dtype=np.int32),
+                           rng.integers(-255, 256, size=(100000, 8)).astype(np.int32)])
+    out, adds = butterfly_host(vecs)
+    assert adds == 14
+    assert np.array_equal(out.astype(np.int64), vecs.astype(np.int64) @ T.T)
+    # inverse after forward, with 64 D^2 applied between: T^T (64 D^2) T x = 64 x
+    a = oracle.scale_exponents()
+    back, _ = butterfly_host((out.astype(np.int64) * (64 >> a)).astype(np.int32), inverse=True)
+    assert np.array_equal(back.astype(np.int64), 64 * vecs.astype(np.int64))
+
+
+def test_create_without_device_fails_cleanly(lib):
+    import ctypes
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    assert lib.adct_create(ctypes.byref(h), 0) != 0
+    assert not h.value
+
+
+def test_make_quant_validates():
+    from paper_1702_00817_gb300.codec import make_quant
+    q = make_quant(1, np.arange(1, 65), 10)
+    assert q.mode == 1 and q.r == 10 and list(q.Q)[:3] == [1, 2, 3]
+    with pytest.raises(ValueError):
+        make_quant(1, np.arange(1, 10))
+    with pytest.raises(ValueError):
+        make_quant(1, np.full(64, 70000))
