@@ -98,19 +98,22 @@ typedef struct {
 } adct_quant;
 
 /*
- * Launch shape of the integer kernels.  Zero fields take the defaults.
- *   threads_per_cta   multiple of 32 in [32, 1024]
- *   ctas_per_sm       resident CTAs per SM the persistent grid is sized for (1..32)
- *   blocks_per_thread 1 or 2 8x8 blocks per thread (2 needs 16-byte aligned rows)
- *   stage_coef        0: each thread stores its coefficients directly;
+ * Launch shape of the integer kernels (one 8x8 block per thread, each warp a
+ * tile of 32 blocks, 12 KB of shared memory per warp).  Zero fields of
+ * threads_per_cta / ctas_per_sm keep the current value.
+ *   threads_per_cta   multiple of 32 in [32, 128]
+ *   ctas_per_sm       CTAs per SM the persistent grid is sized for (1..32); capped
+ *                     at the number that can be resident at once
+ *   stage_coef        0: each thread stores its 128 coefficient bytes directly;
  *                     1: coefficients are staged through shared memory and
- *                        stored by the warp as contiguous 512-byte rows
+ *                        written by the warp as contiguous 512-byte stores
+ *   reserved          must be 0
  */
 typedef struct {
   int32_t threads_per_cta;
   int32_t ctas_per_sm;
-  int32_t blocks_per_thread;
   int32_t stage_coef;
+  int32_t reserved;
 } adct_launch;
 
 /* Create a context on CUDA device `device` (checks for compute capability 10.3).
@@ -191,7 +194,7 @@ adct_status adct_roundtrip_graph(adct_context* ctx, const adct_image* imgs, int3
 
 /*
  * Autotune the launch shape for this batch: times each candidate (threads per
- * CTA x CTAs per SM x blocks per thread x coefficient staging) with CUDA events
+ * CTA x CTAs per SM x coefficient staging) with CUDA events
  * over `reps` round trips after one warm-up, keeps the fastest in ctx and
  * writes it to *best, its mean time in microseconds to *best_us (nullable).
  * Runs synchronously on `stream`; outputs of the batch are overwritten.

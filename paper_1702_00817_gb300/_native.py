@@ -53,8 +53,8 @@ class adct_launch(ctypes.Structure):
     _fields_ = [
         ("threads_per_cta", ctypes.c_int32),
         ("ctas_per_sm", ctypes.c_int32),
-        ("blocks_per_thread", ctypes.c_int32),
         ("stage_coef", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 

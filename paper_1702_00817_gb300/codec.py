@@ -174,8 +174,8 @@ class Codec:
         N.check(st, self.ctx, "adct_roundtrip_graph")
         return bool(rep.value)
 
-    def set_launch(self, threads_per_cta=0, ctas_per_sm=0, blocks_per_thread=0, stage_coef=0):
-        l = N.adct_launch(threads_per_cta, ctas_per_sm, blocks_per_thread, stage_coef)
+    def set_launch(self, threads_per_cta=0, ctas_per_sm=0, stage_coef=1):
+        l = N.adct_launch(threads_per_cta, ctas_per_sm, stage_coef, 0)
         N.check(self.lib.adct_set_launch(self.ctx, ctypes.byref(l)), self.ctx, "adct_set_launch")
 
     def get_launch(self) -> dict:

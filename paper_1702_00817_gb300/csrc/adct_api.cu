@@ -52,7 +52,7 @@ struct PipeSlot {
 struct adct_context {
   int device = 0;
   int sm_count = 0;
-  LaunchShape shape{256, 2, 1, 0};
+  LaunchShape shape{128, 3, 1};
   std::string last_error;
   Slot slots[kSlots];
   int next_slot = 0;
@@ -140,28 +140,44 @@ void zigzag_rank(int rank[64]) {
 bool uses_step(int mode) { return mode == ADCT_Q_STEP || mode == ADCT_Q_STEP_ZONAL; }
 bool uses_zonal(int mode) { return mode == ADCT_Q_ZONAL || mode == ADCT_Q_STEP_ZONAL; }
 
-adct_status build_quant(adct_context* ctx, const adct_quant* q, QuantParams& qp) {
-  if (!q) return fail(ctx, ADCT_ERR_INVALID_ARG, "quant is NULL");
+// Per-position quantiser constants (see QuantParams).  pixel_input: Z is
+// computed from raw pixels, so Z_00 carries +8192 that the constants remove.
+adct_status build_quant(adct_context* ctx, const adct_quant* q, bool pixel_input, QuantParams& qp, bool& evenq) {
+  adct_quant none{};
+  none.mode = ADCT_Q_NONE;
+  if (!q) q = &none;
   if (q->mode < ADCT_Q_NONE || q->mode > ADCT_Q_STEP_ZONAL) return fail(ctx, ADCT_ERR_INVALID_ARG, "bad quant mode");
   if (uses_zonal(q->mode) && (q->r < 0 || q->r > 64)) return fail(ctx, ADCT_ERR_INVALID_ARG, "r outside 0..64");
   int rank[64];
   zigzag_rank(rank);
+  evenq = false;
   for (int k = 0; k < 64; ++k) {
     const int i = k / 8, j = k % 8;
-    uint32_t Q = 1;
-    if (uses_step(q->mode)) {
-      Q = q->Q[k];
-      if (Q < 1) return fail(ctx, ADCT_ERR_INVALID_ARG, "Q entry below 1");
-    }
-    if (Q == 1) {
-      qp.magic[k] = 0xFFFFFFFFu;
-      qp.bias[k] = 1u;
-    } else {
-      qp.magic[k] = (uint32_t)(((1ull << 32) + Q - 1) / Q);
-      qp.bias[k] = Q / 2;
-    }
-    qp.w[k] = (int32_t)(Q << (6 - scale_exp(i) - scale_exp(j)));
+    const int shift = 6 - scale_exp(i) - scale_exp(j);
+    const int32_t zoff = (pixel_input && k == 0) ? -8192 : 0;
     qp.keep[k] = (!uses_zonal(q->mode) || rank[k] < q->r) ? -1 : 0;
+    qp.c[k] = 0;
+    qp.magic[k] = 0;
+    qp.K[k] = 0;
+    qp.sflag[k] = 0;
+    const int32_t bias = (k == 0) ? 8224 : 0;  // 32 + 128 * 64
+    if (!uses_step(q->mode)) {
+      qp.w[k] = 1 << shift;
+      qp.kw[k] = bias;
+      continue;
+    }
+    const uint32_t Q = q->Q[k];
+    if (Q < 1) return fail(ctx, ADCT_ERR_INVALID_ARG, "Q entry below 1");
+    qp.w[k] = (int32_t)(Q << shift);
+    qp.kw[k] = bias;
+    if (Q > 16384) continue;  // |Z| <= 8192 < Q / 2: every coefficient rounds to 0
+    const int32_t K = (int32_t)((8193 + Q - 1) / Q);
+    qp.K[k] = K;
+    qp.c[k] = zoff + (int32_t)(Q / 2) + K * (int32_t)Q + (Q == 1 ? 1 : 0);
+    qp.magic[k] = (Q == 1) ? 0xFFFFFFFFu : (uint32_t)(((1ull << 32) + Q - 1) / Q);
+    qp.sflag[k] = (Q % 2 == 0) ? -1 : 0;
+    if (Q % 2 == 0) evenq = true;
+    qp.kw[k] = (int32_t)((uint32_t)bias - (uint32_t)K * (uint32_t)qp.w[k]);
   }
   return ADCT_OK;
 }
@@ -170,12 +186,11 @@ enum Need { NEED_SRC = 1, NEED_DST = 2, NEED_COEF = 4 };
 
 // Validates the images and builds the plane descriptor table.
 adct_status build_planes(adct_context* ctx, const adct_image* imgs, int32_t n, int need, std::vector<PlaneDesc>& planes,
-                         std::vector<int64_t>& starts, bool& pitch16) {
+                         std::vector<int64_t>& starts) {
   if (n < 0) return fail(ctx, ADCT_ERR_INVALID_ARG, "negative image count");
   if (n > 0 && !imgs) return fail(ctx, ADCT_ERR_INVALID_ARG, "imgs is NULL");
   planes.clear();
   starts.clear();
-  pitch16 = true;
   int64_t total = 0;
   for (int32_t m = 0; m < n; ++m) {
     const adct_image& im = imgs[m];
@@ -192,9 +207,6 @@ adct_status build_planes(adct_context* ctx, const adct_image* imgs, int32_t n, i
     if ((uintptr_t)im.src % 8 || (uintptr_t)im.dst % 8 || im.pitch % 8 ||
         (im.channels > 1 && im.plane_stride % 8) || (uintptr_t)im.coef % 16)
       return fail(ctx, ADCT_ERR_ALIGN, "src/dst/pitch/plane_stride need 8-byte, coef 16-byte alignment" + at);
-    if ((uintptr_t)im.src % 16 || (uintptr_t)im.dst % 16 || im.pitch % 16 ||
-        (im.channels > 1 && im.plane_stride % 16) || (im.width / 8) % 2)
-      pitch16 = false;
     const int32_t wb = im.width / 8, hb = im.height / 8;
     const int64_t nb = (int64_t)wb * hb;
     for (int32_t c = 0; c < im.channels; ++c) {
@@ -254,9 +266,9 @@ adct_status acquire_slot(adct_context* ctx, size_t bytes, Slot** out) {
 }
 
 adct_status check_shape(adct_context* ctx, const LaunchShape& sh) {
-  if (sh.threads < 32 || sh.threads > 256 || sh.threads % 32 || sh.ctas_per_sm < 1 || sh.ctas_per_sm > 32 ||
-      sh.blocks_per_thread != 1 || sh.stage_coef != 0)
-    return fail(ctx, ADCT_ERR_UNSUPPORTED, "launch shape not supported");
+  if (sh.threads < 32 || sh.threads > 128 || sh.threads % 32 || sh.ctas_per_sm < 1 || sh.ctas_per_sm > 32 ||
+      (sh.stage_coef != 0 && sh.stage_coef != 1))
+    return fail(ctx, ADCT_ERR_INVALID_ARG, "launch shape out of range");
   return ADCT_OK;
 }
 
@@ -291,14 +303,14 @@ adct_status run_codec(adct_context* ctx, const adct_image* imgs, int32_t n, cons
   CodecLaunch cl{};
   cl.kind = kind;
   cl.qmode = QM_NONE;
-  if (kind != K_FORWARD) {
-    st = build_quant(ctx, quant, cl.qp);
-    if (st != ADCT_OK) return st;
-    cl.qmode = (kind == K_INVERSE) ? QM_NONE : quant->mode;
-  }
+  if (kind != K_FORWARD && !quant) return fail(ctx, ADCT_ERR_INVALID_ARG, "quant is NULL");
+  const bool pixel_input = (kind != K_QUANTISE && kind != K_INVERSE);
+  st = build_quant(ctx, kind == K_FORWARD ? nullptr : quant, pixel_input, cl.qp, cl.evenq);
+  if (st != ADCT_OK) return st;
+  if (kind != K_FORWARD && kind != K_INVERSE) cl.qmode = quant->mode;
   std::vector<PlaneDesc> planes;
   std::vector<int64_t> starts;
-  st = build_planes(ctx, imgs, n, need_for_kind(kind), planes, starts, cl.pitch16);
+  st = build_planes(ctx, imgs, n, need_for_kind(kind), planes, starts);
   if (st != ADCT_OK) return st;
   cl.total = starts.back();
   if (cl.total == 0) return ADCT_OK;
@@ -448,9 +460,9 @@ void adct_destroy(adct_context* ctx) {
 adct_status adct_set_launch(adct_context* ctx, const adct_launch* l) {
   if (!ctx || !l) return ADCT_ERR_INVALID_ARG;
   LaunchShape sh = ctx->shape;
+  if (l->reserved) return fail(ctx, ADCT_ERR_INVALID_ARG, "reserved must be 0");
   if (l->threads_per_cta) sh.threads = l->threads_per_cta;
   if (l->ctas_per_sm) sh.ctas_per_sm = l->ctas_per_sm;
-  if (l->blocks_per_thread) sh.blocks_per_thread = l->blocks_per_thread;
   sh.stage_coef = l->stage_coef;
   adct_status st = check_shape(ctx, sh);
   if (st != ADCT_OK) return st;
@@ -462,8 +474,8 @@ adct_status adct_get_launch(adct_context* ctx, adct_launch* l) {
   if (!ctx || !l) return ADCT_ERR_INVALID_ARG;
   l->threads_per_cta = ctx->shape.threads;
   l->ctas_per_sm = ctx->shape.ctas_per_sm;
-  l->blocks_per_thread = ctx->shape.blocks_per_thread;
   l->stage_coef = ctx->shape.stage_coef;
+  l->reserved = 0;
   return ADCT_OK;
 }
 
@@ -556,12 +568,13 @@ adct_status adct_roundtrip_graph(adct_context* ctx, const adct_image* imgs, int3
   if (st != ADCT_OK) return st;
   CodecLaunch cl{};
   cl.kind = kind;
-  st = build_quant(ctx, quant, cl.qp);
+  if (!quant) return fail(ctx, ADCT_ERR_INVALID_ARG, "quant is NULL");
+  st = build_quant(ctx, quant, true, cl.qp, cl.evenq);
   if (st != ADCT_OK) return st;
   cl.qmode = quant->mode;
   std::vector<PlaneDesc> planes;
   std::vector<int64_t> starts;
-  st = build_planes(ctx, imgs, n, need_for_kind(kind), planes, starts, cl.pitch16);
+  st = build_planes(ctx, imgs, n, need_for_kind(kind), planes, starts);
   if (st != ADCT_OK) return st;
   cl.total = starts.back();
   if (cl.total == 0) return ADCT_OK;
@@ -630,15 +643,17 @@ adct_status adct_autotune(adct_context* ctx, const adct_image* imgs, int32_t n, 
   cudaEvent_t e0, e1;
   ADCT_CUDA(ctx, cudaEventCreate(&e0));
   ADCT_CUDA(ctx, cudaEventCreate(&e1));
-  const int threads_c[] = {64, 128, 256};
-  const int ctas_c[] = {1, 2, 3, 4, 6, 8, 12, 16};
+  const int threads_c[] = {32, 64, 96, 128};
+  const int ctas_c[] = {2, 3, 4, 5, 6, 8, 10, 12};
   float best_t = 1e30f;
   LaunchShape best_sh = ctx->shape;
   adct_status result = ADCT_OK;
+  for (int stage : {0, 1})
   for (int th : threads_c) {
     for (int cps : ctas_c) {
       if (th * cps > 2048) continue;
-      LaunchShape sh{th, cps, 1, 0};
+      if ((size_t)cps * codec_smem_bytes(LaunchShape{th, cps, stage}) > 200 * 1024) continue;  // shared memory per SM
+      LaunchShape sh{th, cps, stage};
       adct_status st = run_codec(ctx, imgs, n, quant, kind, s, sh);  // warm-up
       if (st != ADCT_OK) { result = st; goto done; }
       cudaEventRecord(e0, s);
@@ -657,8 +672,8 @@ adct_status adct_autotune(adct_context* ctx, const adct_image* imgs, int32_t n, 
   ctx->shape = best_sh;
   best->threads_per_cta = best_sh.threads;
   best->ctas_per_sm = best_sh.ctas_per_sm;
-  best->blocks_per_thread = best_sh.blocks_per_thread;
   best->stage_coef = best_sh.stage_coef;
+  best->reserved = 0;
   if (best_us) *best_us = best_t;
 done:
   cudaEventDestroy(e0);

@@ -1,14 +1,35 @@
 // Integer codec kernels for sm_103a: the blockwise 2D 14-addition transform
-// (Sec. 2 fast algorithm; Sec. 3 8x8 blocks), the D^2-merged quantiser and
-// the inverse, as one persistent kernel over a flattened block index.
+// (Sec. 2 fast algorithm T = P A3 A2 A1; Sec. 3 8x8 blocks), the D^2-merged
+// quantiser and the inverse, as one persistent kernel over a flattened block
+// index.  The path is add-only and bound by HBM bytes, so no tensor cores.
 //
-// Work split: the grid is sized to the SMs (persistent); each warp owns a
-// contiguous chunk of the flat block index and walks it 32 blocks at a time,
-// one 8x8 block per lane, so every row load of a warp reads 32 adjacent
-// blocks = 256 contiguous bytes of an image row.  The 8x8 block lives in 64
-// registers; both passes of the separable transform and the transpose
-// between them are register renaming.  The path is add-only and bound by
-// HBM bytes, so no tensor cores are involved.
+// Work split.  The grid is sized to the SMs; each warp owns a contiguous
+// chunk of the flat block index and walks it in tiles of 32 blocks, one 8x8
+// block per lane.  An 8x8 block lives in 64 registers, so both passes of the
+// separable transform and the transpose between them are register renaming.
+//
+// Memory pipeline per warp (all in the warp's slice of shared memory):
+//   - the next tile's input is prefetched with cp.async while the current one
+//     is computed (pixels: each lane copies its block's 8 rows, 8 bytes each,
+//     so one copy instruction of the warp moves 256 contiguous bytes;
+//     coefficients: the warp copies the tile's contiguous 4 KB, 512 bytes per
+//     instruction, into a 16-byte-chunk XOR swizzle);
+//   - quantised coefficients of a full tile are staged in the same swizzle and
+//     written back as 512-byte contiguous warp stores (one L2 request per
+//     128-byte line instead of one per 16 bytes);
+//   - reconstructed pixels are stored directly (256 contiguous bytes per warp
+//     instruction already).
+//
+// Arithmetic per block (one lane):
+//   forward  raw bytes -> 8 row butterflies -> 8 column butterflies (Z + 8192 e0e0^T);
+//   quantise n = Z + c (bias, offset and level shift folded into one constant,
+//            added by the last butterfly stage), m = umulhi(n, magic) = floor(n / Q),
+//            q = m - K; for tables with even steps the sign of Z moves the bias by
+//            one so that ties round away from zero;
+//   dequant  S = q w, w = Q 2^(6 - a_i - a_j) (D^2 merged), + 8224 at (0, 0)
+//            (rounding and level shift of every pixel: T^T e0 = 1);
+//   inverse  8 column then 8 row transposed butterflies;
+//   output   pixel = saturate_u8(R >> 6).
 #include <cuda_runtime.h>
 
 #include "adct_internal.h"
@@ -16,17 +37,49 @@
 namespace adct {
 namespace {
 
-constexpr int kMaxThreads = 256;
+constexpr int kMaxThreads = 128;  // with 3 CTAs per SM: up to 168 registers per thread
+constexpr int kTileBytesIn = 4096;   // one input stage: 32 blocks of coefficients (pixels use 2 KB of it)
+constexpr int kTileBytesOut = 4096;  // output staging: 32 blocks of int16 coefficients
 
 __device__ __forceinline__ int32_t sext_lo16(uint32_t w) { return (int32_t)(int16_t)(w & 0xFFFFu); }
 __device__ __forceinline__ int32_t sext_hi16(uint32_t w) { return ((int32_t)w) >> 16; }
 __device__ __forceinline__ uint32_t pack16(int32_t lo, int32_t hi) {
   return __byte_perm((uint32_t)lo, (uint32_t)hi, 0x5410);
 }
-__device__ __forceinline__ uint32_t clamp_u8(int32_t r) { return (uint32_t)min(max(r >> 6, 0), 255); }
-__device__ __forceinline__ uint32_t pack_u8x4(uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-  return __byte_perm(__byte_perm(a, b, 0x0040), __byte_perm(c, d, 0x0040), 0x5410);
+// (c << 16) | (sat_u8(a) << 8) | sat_u8(b)
+__device__ __forceinline__ uint32_t cvt_pack_u8(int32_t a, int32_t b, uint32_t c) {
+  uint32_t d;
+  asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
 }
+// four reconstructed values (R + 8224) -> four saturated pixels, p0 in the lowest byte
+__device__ __forceinline__ uint32_t pixels4(int32_t r0, int32_t r1, int32_t r2, int32_t r3) {
+  const uint32_t hi = cvt_pack_u8(r3 >> 6, r2 >> 6, 0u);
+  return cvt_pack_u8(r1 >> 6, r0 >> 6, hi);
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// 16-byte chunk c of block b inside a 32-block coefficient tile, XOR-swizzled
+// so that 8 consecutive lanes touching one chunk each hit distinct banks.
+__device__ __forceinline__ int swz(int b, int c) { return b * 128 + ((c ^ (b & 7)) << 4); }
+
+// Reconstruction offset carried by S_00: 32 (rounding of R / 64) + 128 * 64
+// (level shift); T^T e0 = 1 spreads it to every pixel of the block.
+constexpr int32_t kDcBias = 32 + 128 * 64;
 
 template <int KIND>
 struct KindTraits {
@@ -36,155 +89,311 @@ struct KindTraits {
   static constexpr bool inv = (KIND == K_INVERSE || KIND == K_RT_FULL || KIND == K_RT_PIX);
 };
 
-template <int KIND, int QMODE>
-__global__ void __launch_bounds__(kMaxThreads, 2)
+// Position of one lane's block: plane index and block coordinates (by, bx);
+// plane < 0 past the end of the warp's chunk.  Addresses are recomputed from
+// the plane descriptor (an L1 hit) when needed, which keeps the per-lane state
+// of the two tiles in flight to six registers.
+struct Pos {
+  int plane;
+  uint32_t by, bx;
+};
+
+__device__ __forceinline__ int64_t pix_off(const PlaneDesc* d, const Pos& q) {
+  return (int64_t)(8 * q.by) * __ldg(&d->pitch) + 8 * q.bx;
+}
+__device__ __forceinline__ const uint8_t* src_of(const PlaneDesc* d) {
+  return (const uint8_t*)__ldg((const unsigned long long*)&d->src);
+}
+__device__ __forceinline__ uint8_t* dst_of(const PlaneDesc* d) {
+  return (uint8_t*)__ldg((const unsigned long long*)&d->dst);
+}
+__device__ __forceinline__ int16_t* coef_of(const PlaneDesc* d, const Pos& q) {
+  const int16_t* c = (const int16_t*)__ldg((const unsigned long long*)&d->coef);
+  return (int16_t*)c + ((int64_t)q.by * __ldg(&d->wb) + q.bx) * 64;
+}
+
+// Plane cursor of one lane: the flat index only grows, so the plane index
+// only moves forward.  Offsets are 32-bit, relative to the warp's chunk start.
+struct Cursor {
+  int p;
+  int32_t first, next_start;  // plane p spans [first, next_start) relative to the chunk start
+
+  __device__ __forceinline__ Pos locate(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts,
+                                        int64_t begin, int32_t r, int32_t rend) {
+    Pos q;
+    if (r >= rend) {
+      q.plane = -1; q.by = 0; q.bx = 0;
+      return q;
+    }
+    if (r >= next_start) {
+      do {
+        ++p;
+        next_start = (int32_t)min(__ldg(starts + p + 1) - begin, (int64_t)0x7fffffff);
+      } while (r >= next_start);
+      first = (int32_t)(__ldg(starts + p) - begin);
+    }
+    const uint32_t f = (uint32_t)(r - first);
+    const uint32_t wb = (uint32_t)__ldg(&planes[p].wb);
+    q.plane = p;
+    q.by = f / wb;
+    q.bx = f - q.by * wb;
+    return q;
+  }
+};
+
+template <int KIND, int QMODE, bool EVENQ>
+__global__ void __launch_bounds__(kMaxThreads, 3)
 k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts, int32_t nplanes, int64_t total,
-        int64_t chunk, const QuantParams qp) {
+        int64_t chunk, int stage_coef, const QuantParams qp) {
   using KT = KindTraits<KIND>;
+  extern __shared__ __align__(128) uint8_t smem[];
   const int lane = threadIdx.x & 31;
+  const int warp_cta = threadIdx.x >> 5;
+  uint8_t* wsm = smem + warp_cta * (2 * kTileBytesIn + kTileBytesOut);
+  uint8_t* stage_out = wsm + 2 * kTileBytesIn;
+
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t begin = gwarp * chunk;
-  if (begin >= total) return;
+  if (begin >= total) return;  // whole warp exits together
   const int64_t end = min(total, begin + chunk);
 
-  // plane holding `begin`: largest p with starts[p] <= begin
-  int lo = 0, hi = nplanes;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (__ldg(starts + mid) <= begin) lo = mid; else hi = mid;
-  }
-  int p = lo;
-  int64_t next_start = __ldg(starts + p + 1);
-
-  for (int64_t g = begin + lane; g < end; g += 32) {
-    while (g >= next_start) {
-      ++p;
-      next_start = __ldg(starts + p + 1);
+  const int32_t rend = (int32_t)(end - begin);  // chunk length (< 2^31 blocks)
+  Cursor cur;
+  {
+    int lo = 0, hi = nplanes;  // largest p with starts[p] <= begin
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (__ldg(starts + mid) <= begin) lo = mid; else hi = mid;
     }
-    const PlaneDesc* d = planes + p;
-    const int64_t first = __ldg(&d->first);
-    const int32_t wb = __ldg(&d->wb);
-    const uint32_t f = (uint32_t)(g - first);
-    const uint32_t by = f / (uint32_t)wb;
-    const uint32_t bx = f - by * (uint32_t)wb;
-    const int64_t pitch = __ldg(&d->pitch);
-    const int64_t pix_off = (int64_t)(8 * by) * pitch + 8 * bx;
+    cur.p = lo;
+    cur.first = (int32_t)(__ldg(starts + lo) - begin);
+    cur.next_start = (int32_t)min(__ldg(starts + lo + 1) - begin, (int64_t)0x7fffffff);
+  }
 
-    int32_t v[64];
+  // Issue the asynchronous input copies of one tile into stage s.
+  auto issue = [&](int s, const Pos& q) {
+    const uint32_t sa = smem_addr(wsm + s * kTileBytesIn);
     if (KT::in_pix) {
-      const uint8_t* s = (const uint8_t*)__ldg((const unsigned long long*)&d->src) + pix_off;
-      uint2 w[8];
+      if (q.plane >= 0) {
+        const PlaneDesc* d = planes + q.plane;
+        const int64_t pitch = __ldg(&d->pitch);
+        const uint8_t* src = src_of(d) + (int64_t)(8 * q.by) * pitch + 8 * q.bx;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) w[i] = __ldcs((const uint2*)(s + i * pitch));
+        for (int i = 0; i < 8; ++i) cp_async8(sa + (i * 32 + lane) * 8, src + i * pitch);
+      }
+    } else {
+      // Coefficients: lane copies 16-byte chunk c of block b (512 contiguous
+      // bytes per warp instruction when the tile lies in one plane).
+      const int16_t* mine = q.plane >= 0 ? coef_of(planes + q.plane, q) : nullptr;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
+      for (int k = 0; k < 8; ++k) {
+        const int b = 4 * k + (lane >> 3), c = lane & 7;
+        const int16_t* cb = (const int16_t*)__shfl_sync(0xffffffffu, (unsigned long long)mine, b);
+        if (cb) cp_async16(sa + swz(b, c), cb + 8 * c);
+      }
+    }
+    cp_async_commit();
+  };
+
+  Pos p_cur = cur.locate(planes, starts, begin, lane, rend);
+  issue(0, p_cur);
+  int s = 0;
+  for (int32_t base = 0; base < rend; base += 32, s ^= 1) {
+    const int32_t nbase = base + 32;
+    __syncwarp();  // every lane is done reading stage s ^ 1 before it is refilled
+    const Pos p_next = cur.locate(planes, starts, begin, nbase + lane, rend);
+    if (nbase < rend) issue(s ^ 1, p_next);
+    else cp_async_commit();
+    cp_async_wait<1>();
+    __syncwarp();
+
+    const bool active = p_cur.plane >= 0;
+    const PlaneDesc* d = planes + (active ? p_cur.plane : 0);
+    int32_t v[64];
+    if (active) {
+      if (KT::in_pix) {
+        const uint2* st = (const uint2*)(wsm + s * kTileBytesIn);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          v[8 * i + j] = (int32_t)__byte_perm(w[i].x, 0u, 0x4440 | j);
-          v[8 * i + 4 + j] = (int32_t)__byte_perm(w[i].y, 0u, 0x4440 | j);
+        for (int i = 0; i < 8; ++i) {
+          const uint2 w = st[i * 32 + lane];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            v[8 * i + j] = (int32_t)__byte_perm(w.x, 0u, 0x4440 | j);
+            v[8 * i + 4 + j] = (int32_t)__byte_perm(w.y, 0u, 0x4440 | j);
+          }
+        }
+        fwd2d(v);  // Z + 8192 e0 e0^T (raw pixels; the level shift lives in the constants)
+      } else {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int4 u = *(const int4*)(wsm + s * kTileBytesIn + swz(lane, t));
+          v[8 * t + 0] = sext_lo16(u.x); v[8 * t + 1] = sext_hi16(u.x);
+          v[8 * t + 2] = sext_lo16(u.y); v[8 * t + 3] = sext_hi16(u.y);
+          v[8 * t + 4] = sext_lo16(u.z); v[8 * t + 5] = sext_hi16(u.z);
+          v[8 * t + 6] = sext_lo16(u.w); v[8 * t + 7] = sext_hi16(u.w);
         }
       }
-      fwd2d(v);
-      v[0] -= 8192;  // level shift: T (X - 128) T^T = T X T^T - 8192 e0 e0^T (T 1 = 8 e0)
-    } else {
-      const int16_t* c = (const int16_t*)__ldg((const unsigned long long*)&d->coef) + (int64_t)f * 64;
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int4 u = __ldcs((const int4*)c + t);
-        v[8 * t + 0] = sext_lo16(u.x); v[8 * t + 1] = sext_hi16(u.x);
-        v[8 * t + 2] = sext_lo16(u.y); v[8 * t + 3] = sext_hi16(u.y);
-        v[8 * t + 4] = sext_lo16(u.z); v[8 * t + 5] = sext_hi16(u.z);
-        v[8 * t + 6] = sext_lo16(u.w); v[8 * t + 7] = sext_hi16(u.w);
-      }
-    }
 
-    if (KT::quant) {
-#pragma unroll
-      for (int k = 0; k < 64; ++k) v[k] = quantise1<QMODE>(v[k], qp, k);
-    }
-
-    if (KT::write_coef) {
-      int16_t* c = (int16_t*)__ldg((const unsigned long long*)&d->coef) + (int64_t)f * 64;
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        int4 u;
-        u.x = (int)pack16(v[8 * t + 0], v[8 * t + 1]);
-        u.y = (int)pack16(v[8 * t + 2], v[8 * t + 3]);
-        u.z = (int)pack16(v[8 * t + 4], v[8 * t + 5]);
-        u.w = (int)pack16(v[8 * t + 6], v[8 * t + 7]);
-        __stcs((int4*)c + t, u);
-      }
-    }
-
-    if (KT::inv) {
-#pragma unroll
-      for (int k = 0; k < 64; ++k) v[k] *= qp.w[k];
-      // +32 rounding and +128 level shift on every pixel: T^T e0 = 1, so
-      // adding 32 + 128 * 64 to S_00 adds it to all of R.
-      v[0] += 8224;
-      inv2d(v);
-      uint8_t* o = (uint8_t*)__ldg((const unsigned long long*)&d->dst) + pix_off;
+      // ---- quantise (q, stored row by row) and dequantise in place (v <- S) ----
+      // S = q * w with w = Q 2^(6 - a_i - a_j) (D^2 merged), plus kDcBias at
+      // (0, 0).  For STEP it is formed from m directly (S = m * w + kw, kw =
+      // -K * w (+ kDcBias)), independent of the q = m - K that goes to memory.
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        uint2 w;
-        w.x = pack_u8x4(clamp_u8(v[8 * i + 0]), clamp_u8(v[8 * i + 1]), clamp_u8(v[8 * i + 2]), clamp_u8(v[8 * i + 3]));
-        w.y = pack_u8x4(clamp_u8(v[8 * i + 4]), clamp_u8(v[8 * i + 5]), clamp_u8(v[8 * i + 6]), clamp_u8(v[8 * i + 7]));
-        __stcs((uint2*)(o + i * pitch), w);
+        int32_t q[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int k = 8 * i + j;
+          const int32_t bias = (k == 0) ? kDcBias : 0;
+          const int32_t z = v[k];  // raw: Z + 8192 at (0, 0) when the input was pixels
+          // T (X - 128) T^T = T X T^T - 8192 e0 e0^T  (T 1 = 8 e0)
+          const int32_t zoff = (KT::in_pix && k == 0) ? -8192 : 0;
+          if (KIND == K_INVERSE) {
+            q[j] = z;
+            v[k] = (int32_t)((uint32_t)z * (uint32_t)qp.w[k] + (uint32_t)bias);
+          } else if (QMODE == QM_STEP || QMODE == QM_STEP_ZONAL) {
+            int32_t n = z + qp.c[k];
+            if (EVENQ) n += ((z + zoff) >> 31) & qp.sflag[k];
+            const uint32_t m = __umulhi((uint32_t)n, qp.magic[k]);
+            int32_t qq = (int32_t)m - qp.K[k];
+            if (QMODE == QM_STEP_ZONAL) qq &= qp.keep[k];
+            q[j] = qq;
+            if (KT::inv)
+              v[k] = (QMODE == QM_STEP_ZONAL) ? (int32_t)((uint32_t)qq * (uint32_t)qp.w[k] + (uint32_t)bias)
+                                              : (int32_t)(m * (uint32_t)qp.w[k] + (uint32_t)qp.kw[k]);
+          } else {
+            int32_t qq = z + zoff;  // the true coefficient
+            if (QMODE == QM_ZONAL) qq &= qp.keep[k];
+            q[j] = qq;
+            if (KT::inv) v[k] = (int32_t)((uint32_t)qq * (uint32_t)qp.w[k] + (uint32_t)bias);
+          }
+        }
+        if (KT::write_coef) {
+          int4 u;
+          u.x = (int)pack16(q[0], q[1]);
+          u.y = (int)pack16(q[2], q[3]);
+          u.z = (int)pack16(q[4], q[5]);
+          u.w = (int)pack16(q[6], q[7]);
+          if (stage_coef) *(int4*)(stage_out + swz(lane, i)) = u;
+          else __stcs((int4*)coef_of(d, p_cur) + i, u);
+        }
+      }
+
+      // ---- inverse (8 column, then 8 row transposed butterflies) and output ----
+      if (KT::inv) {
+        inv2d(v);
+        const int64_t pitch = __ldg(&d->pitch);
+        uint8_t* o = dst_of(d) + (int64_t)(8 * p_cur.by) * pitch + 8 * p_cur.bx;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          uint2 w;
+          w.x = pixels4(v[8 * i + 0], v[8 * i + 1], v[8 * i + 2], v[8 * i + 3]);
+          w.y = pixels4(v[8 * i + 4], v[8 * i + 5], v[8 * i + 6], v[8 * i + 7]);
+          __stcs((uint2*)(o + i * pitch), w);
+        }
       }
     }
+
+    if (KT::write_coef && stage_coef) {
+      // Write the staged tile back with 512-byte warp stores.  The blocks of a
+      // plane are contiguous in coef, so when every active lane is in lane 0's
+      // plane the tile is one contiguous range of 128 bytes per active block.
+      __syncwarp();
+      const int plane0 = __shfl_sync(0xffffffffu, p_cur.plane, 0);
+      const unsigned act = __ballot_sync(0xffffffffu, active);
+      int16_t* mine = active ? coef_of(d, p_cur) : nullptr;
+      if (__all_sync(0xffffffffu, !active || p_cur.plane == plane0)) {
+        int16_t* cbase = (int16_t*)__shfl_sync(0xffffffffu, (unsigned long long)mine, 0);
+        const int nact = __popc(act);  // active lanes are a prefix of the warp
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int b = 4 * k + (lane >> 3), c = lane & 7;
+          if (b < nact) __stcs((int4*)(cbase + 64 * b) + c, *(const int4*)(stage_out + swz(b, c)));
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int b = 4 * k + (lane >> 3), c = lane & 7;
+          int16_t* cb = (int16_t*)__shfl_sync(0xffffffffu, (unsigned long long)mine, b);
+          if (cb) __stcs((int4*)cb + c, *(const int4*)(stage_out + swz(b, c)));
+        }
+      }
+      __syncwarp();
+    }
+    p_cur = p_next;
   }
+  cp_async_wait<0>();
 }
 
-using KernelFn = void (*)(const PlaneDesc*, const int64_t*, int32_t, int64_t, int64_t, const QuantParams);
+using KernelFn = void (*)(const PlaneDesc*, const int64_t*, int32_t, int64_t, int64_t, int, const QuantParams);
 
-template <int KIND>
+template <int KIND, bool EVENQ>
 KernelFn pick_mode(int qmode) {
   switch (qmode) {
-    case QM_STEP: return k_codec<KIND, QM_STEP>;
-    case QM_ZONAL: return k_codec<KIND, QM_ZONAL>;
-    case QM_STEP_ZONAL: return k_codec<KIND, QM_STEP_ZONAL>;
-    default: return k_codec<KIND, QM_NONE>;
+    case QM_STEP: return k_codec<KIND, QM_STEP, EVENQ>;
+    case QM_ZONAL: return k_codec<KIND, QM_ZONAL, false>;
+    case QM_STEP_ZONAL: return k_codec<KIND, QM_STEP_ZONAL, EVENQ>;
+    default: return k_codec<KIND, QM_NONE, false>;
   }
 }
 
-KernelFn pick_kernel(int kind, int qmode) {
+template <bool EVENQ>
+KernelFn pick_kernel_q(int kind, int qmode) {
   switch (kind) {
-    case K_FORWARD: return k_codec<K_FORWARD, QM_NONE>;
+    case K_FORWARD: return k_codec<K_FORWARD, QM_NONE, false>;
     case K_QUANTISE:
       switch (qmode) {
-        case QM_STEP: return k_codec<K_QUANTISE, QM_STEP>;
-        case QM_ZONAL: return k_codec<K_QUANTISE, QM_ZONAL>;
-        case QM_STEP_ZONAL: return k_codec<K_QUANTISE, QM_STEP_ZONAL>;
+        case QM_STEP: return k_codec<K_QUANTISE, QM_STEP, EVENQ>;
+        case QM_ZONAL: return k_codec<K_QUANTISE, QM_ZONAL, false>;
+        case QM_STEP_ZONAL: return k_codec<K_QUANTISE, QM_STEP_ZONAL, EVENQ>;
         default: return nullptr;
       }
-    case K_INVERSE: return k_codec<K_INVERSE, QM_NONE>;
-    case K_RT_FULL: return pick_mode<K_RT_FULL>(qmode);
-    case K_RT_PIX: return pick_mode<K_RT_PIX>(qmode);
-    case K_RT_COEF: return pick_mode<K_RT_COEF>(qmode);
+    case K_INVERSE: return k_codec<K_INVERSE, QM_NONE, false>;
+    case K_RT_FULL: return pick_mode<K_RT_FULL, EVENQ>(qmode);
+    case K_RT_PIX: return pick_mode<K_RT_PIX, EVENQ>(qmode);
+    case K_RT_COEF: return pick_mode<K_RT_COEF, EVENQ>(qmode);
     default: return nullptr;
   }
 }
 
+KernelFn pick_kernel(int kind, int qmode, bool evenq) {
+  return evenq ? pick_kernel_q<true>(kind, qmode) : pick_kernel_q<false>(kind, qmode);
+}
+
 }  // namespace
 
+size_t codec_smem_bytes(const LaunchShape& shape) {
+  return (size_t)(shape.threads / 32) * (2 * kTileBytesIn + kTileBytesOut);
+}
+
 int codec_grid(const LaunchShape& shape, int sm_count, int64_t total) {
-  const int64_t per_cta = shape.threads;  // one block per lane per pass
-  int64_t want = (total + per_cta - 1) / per_cta;
-  int64_t cap = (int64_t)sm_count * shape.ctas_per_sm;
+  int64_t want = (total + shape.threads - 1) / shape.threads;
+  const int64_t cap = (int64_t)sm_count * shape.ctas_per_sm;
   if (want > cap) want = cap;
   return (int)(want < 1 ? 1 : want);
 }
 
 cudaError_t launch_codec(const CodecLaunch& c, const LaunchShape& shape, int sm_count, cudaStream_t stream) {
   if (c.total <= 0) return cudaSuccess;
-  KernelFn fn = pick_kernel(c.kind, c.qmode);
+  KernelFn fn = pick_kernel(c.kind, c.qmode, c.evenq);
   if (!fn) return cudaErrorInvalidValue;
   if (shape.threads < 32 || shape.threads > kMaxThreads || shape.threads % 32) return cudaErrorInvalidValue;
-  const int grid = codec_grid(shape, sm_count, c.total);
+  const size_t smem = codec_smem_bytes(shape);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  // never size the persistent grid beyond what can be resident at once
+  int resident = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, fn, shape.threads, smem) != cudaSuccess || resident < 1)
+    resident = 1;
+  LaunchShape sh = shape;
+  if (sh.ctas_per_sm > resident) sh.ctas_per_sm = resident;
+  const int grid = codec_grid(sh, sm_count, c.total);
   const int64_t warps = (int64_t)grid * (shape.threads / 32);
   int64_t chunk = (c.total + warps - 1) / warps;
   chunk = (chunk + 31) / 32 * 32;
-  fn<<<grid, shape.threads, 0, stream>>>(c.planes, c.starts, c.nplanes, c.total, chunk, c.qp);
+  fn<<<grid, shape.threads, smem, stream>>>(c.planes, c.starts, c.nplanes, c.total, chunk, shape.stage_coef, c.qp);
   return cudaGetLastError();
 }
 

@@ -44,24 +44,32 @@ __host__ __device__ __forceinline__ void fwd8(V* v) {
   v[4 * S] = c0 - c1;                                               // A3 row 1 -> X4
 }
 
-// Inverse 8-point transform x = T^T X on v[0], v[S], ..., v[7S], in place:
-// the transposed flow graph T^T = A1^T A2^T A3^T P^T = A1 A2 A3 P^T (A1, A2, A3
-// are symmetric), again 14 additions.
+// Inverse 8-point transform x = T^T X from in[0], in[S], ..., in[7S] into
+// out[0], out[S], ..., out[7S] (in and out may alias): the transposed flow
+// graph T^T = A1^T A2^T A3^T P^T = A1 A2 A3 P^T (A1, A2, A3 are symmetric),
+// again 14 additions.  The input type may differ from the output type: the
+// codec passes unevaluated dequantised coefficients (q, w) whose + and - are
+// multiply-adds, which merges the D^2 scaling into the first inverse pass.
+template <int S, class VI, class VO>
+__host__ __device__ __forceinline__ void inv8(const VI* in, VO* out) {
+  const VI X0 = in[0], X1 = in[S], X2 = in[2 * S], X3 = in[3 * S];
+  const VI X4 = in[4 * S], X5 = in[5 * S], X6 = in[6 * S], X7 = in[7 * S];
+  const auto c0 = X0 + X4, c1 = X0 - X4;  // A3 after P^T
+  const auto b0 = c0 + X2, b3 = c0 - X2;  // A2 rows 0, 3
+  const auto b1 = c1 - X6, b2 = c1 + X6;  // A2 rows 1, 2 (A3's sign on row 2 absorbed)
+  out[0] = b0 + X1;                       // A1 (its -1 entries absorbed)
+  out[7 * S] = b0 - X1;
+  out[1 * S] = b1 - X5;
+  out[6 * S] = b1 + X5;
+  out[2 * S] = b2 - X3;
+  out[5 * S] = b2 + X3;
+  out[3 * S] = b3 - X7;
+  out[4 * S] = b3 + X7;
+}
+
 template <int S, class V>
 __host__ __device__ __forceinline__ void inv8(V* v) {
-  const V X0 = v[0], X1 = v[S], X2 = v[2 * S], X3 = v[3 * S];
-  const V X4 = v[4 * S], X5 = v[5 * S], X6 = v[6 * S], X7 = v[7 * S];
-  const V c0 = X0 + X4, c1 = X0 - X4;  // A3 after P^T
-  const V b0 = c0 + X2, b3 = c0 - X2;  // A2 rows 0, 3
-  const V b1 = c1 - X6, b2 = c1 + X6;  // A2 rows 1, 2 (A3's sign on row 2 absorbed)
-  v[0] = b0 + X1;                      // A1 (its -1 entries absorbed)
-  v[7 * S] = b0 - X1;
-  v[1 * S] = b1 - X5;
-  v[6 * S] = b1 + X5;
-  v[2 * S] = b2 - X3;
-  v[5 * S] = b2 + X3;
-  v[3 * S] = b3 - X7;
-  v[4 * S] = b3 + X7;
+  inv8<S, V, V>(v, v);
 }
 
 // Separable 2D forward transform of a row-major 8x8 block: rows, then columns.
@@ -82,6 +90,15 @@ __host__ __device__ __forceinline__ void inv2d(V* v) {
   for (int i = 0; i < 8; ++i) inv8<1>(v + 8 * i);
 }
 
+// Same, reading the column pass's input from `in` (another type).
+template <class VI, class V>
+__host__ __device__ __forceinline__ void inv2d(const VI* in, V* v) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) inv8<8, VI, V>(in + j, v + j);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) inv8<1>(v + 8 * i);
+}
+
 // One plane of the flattened block index.  Planes of a multi-channel image
 // are separate entries.  Block f of the plane (row-major over blocks) sits at
 // src + (8 * (f / wb)) * pitch + 8 * (f % wb); its coefficients at coef + 64 f.
@@ -96,36 +113,32 @@ struct PlaneDesc {
 };
 static_assert(sizeof(PlaneDesc) == 48, "descriptor layout");
 
-// Per-call quantiser constants, passed by value (they live in the kernel
-// parameter bank, so the unrolled per-position accesses are free operands).
-//   magic/bias: floor((|Z| + bias) / Q) == umulhi(|Z| + bias, magic) with
-//               magic = ceil(2^32 / Q), bias = floor(Q / 2) for Q >= 2, and
-//               magic = 2^32 - 1, bias = 1 for Q = 1 (exact for |Z| + bias < 2^16).
-//   w:          dequantisation weight Q_ij * 2^(6 - a_i - a_j) (D^2 merged).
-//   keep:       -1 where the zig-zag rank is below r, 0 elsewhere.
+// Per-call quantiser constants, passed by value: they live in the kernel
+// parameter bank, so the fully unrolled per-position accesses are free
+// instruction operands.  For position k = 8i + j with step Q:
+//   STEP (Q <= 16384): n = Z + c with c = floor(Q/2) + K*Q (+1 when Q = 1), where
+//     K = ceil(8193 / Q) keeps n in [0, 2^16); when Q is even and Z < 0 the
+//     bias drops by one (sflag = -1) so that ties round away from zero.
+//     m = umulhi(n, magic) = floor(n / Q) exactly (magic = ceil(2^32 / Q), or
+//     2^32 - 1 with the +1 above for Q = 1; exact for n < 2^16, Q <= 2^16),
+//     q = m - K = sgn(Z) floor((|Z| + floor(Q/2)) / Q) = round half away from zero of Z / Q.
+//   STEP (Q > 16384): |Z| <= 8192 < Q/2, so q = 0: magic = c = K = 0.
+//   When Z is computed from raw pixels, Z_00 carries +8192 (the level shift
+//   T (X - 128) T^T = T X T^T - 8192 e0 e0^T); c at (0, 0) then includes -8192.
+//   w  : dequantisation weight Q * 2^(6 - a_i - a_j) (D^2 merged), Q = 1 unless STEP;
+//   kw : -K * w, plus 8224 = 32 + 128 * 64 at (0, 0), so that S = m * w + kw
+//        (8224: rounding of R / 64 and level shift of every pixel, T^T e0 = 1).
+//   keep: -1 where the zig-zag rank is below r, 0 elsewhere (ZONAL modes).
 struct QuantParams {
+  int32_t c[64];
   uint32_t magic[64];
-  uint32_t bias[64];
+  int32_t K[64];
+  int32_t sflag[64];
   int32_t w[64];
+  int32_t kw[64];
   int32_t keep[64];
 };
 
 enum QMode { QM_NONE = 0, QM_STEP = 1, QM_ZONAL = 2, QM_STEP_ZONAL = 3 };
-
-// Round half away from zero of z / Q for |z| <= 8192:
-// sgn(z) * floor((|z| + floor(Q/2)) / Q), the division by the magic multiply.
-__device__ __forceinline__ int32_t quant_step(int32_t z, uint32_t magic, uint32_t bias) {
-  const uint32_t mag = (uint32_t)(z < 0 ? -z : z) + bias;
-  const int32_t q = (int32_t)__umulhi(mag, magic);
-  return z < 0 ? -q : q;
-}
-
-template <int QMODE>
-__device__ __forceinline__ int32_t quantise1(int32_t z, const QuantParams& qp, int k) {
-  int32_t q = z;
-  if (QMODE == QM_STEP || QMODE == QM_STEP_ZONAL) q = quant_step(z, qp.magic[k], qp.bias[k]);
-  if (QMODE == QM_ZONAL || QMODE == QM_STEP_ZONAL) q &= qp.keep[k];
-  return q;
-}
 
 }  // namespace adct

@@ -20,10 +20,9 @@ enum Kind {
 };
 
 struct LaunchShape {
-  int threads;            // per CTA, multiple of 32
-  int ctas_per_sm;
-  int blocks_per_thread;  // 1 or 2
-  int stage_coef;         // 0 or 1
+  int threads;      // per CTA, multiple of 32, at most 256
+  int ctas_per_sm;  // persistent grid = SMs x ctas_per_sm (at most)
+  int stage_coef;   // 0: direct 16-byte coefficient stores, 1: staged 512-byte warp stores
 };
 
 struct CodecLaunch {
@@ -33,15 +32,16 @@ struct CodecLaunch {
   int64_t total;            // blocks over all planes
   int kind;                 // Kind
   int qmode;                // QMode (quantiser applied by QUANTISE / RT kinds)
-  bool pitch16;             // every plane's src/dst and pitch are 16-byte aligned, wb even
+  bool evenq;               // the step table has an even step <= 16384 (tie correction needed)
   QuantParams qp;
 };
 
 // Launches the integer codec kernel.  Returns cudaSuccess or the launch error.
 cudaError_t launch_codec(const CodecLaunch& c, const LaunchShape& shape, int sm_count, cudaStream_t stream);
 
-// Largest grid the persistent kernel uses for this shape (CTAs).
+// Largest grid the persistent kernel uses for this shape (CTAs), and its dynamic shared memory.
 int codec_grid(const LaunchShape& shape, int sm_count, int64_t total);
+size_t codec_smem_bytes(const LaunchShape& shape);
 
 // Float variant (Sec. 2 C^ = D T): forward (optionally soft-quantised) and adjoint.
 struct FloatParams {

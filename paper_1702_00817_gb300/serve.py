@@ -1,0 +1,305 @@
+"""Continuous-batching encode/decode server over the codec's C ABI.
+
+Requests arrive at any time (Server.submit); a scheduler thread:
+  1. takes new arrivals into a FIFO queue,
+  2. retires launched batches whose completion events have fired (frees their
+     temporary device memory, fills the results, stamps completion times),
+  3. admits queued requests while the device-memory budget allows (evicting
+     the oldest unreferenced entries of the on-device coefficient store when
+     it must), and
+  4. packs everything admitted in this pass into at most two ragged launches
+     (one encode launch = forward + quantise with q kept on the device, one
+     decode launch = dequantise + inverse) on the next of several CUDA
+     streams, so batches admitted while others are still running overlap on
+     the device.
+Encode: pixels are copied from host memory, the quantised coefficients stay in
+the store under a handle.  Decode: a stored handle is dequantised, inverted
+and the pixels are copied back to host memory.  Results are bit-identical to a
+request run alone (the kernels are per-block and deterministic).
+"""
+from __future__ import annotations
+
+import collections
+import itertools
+import threading
+import time
+from dataclasses import dataclass, field
+
+import torch
+
+from .codec import ADCT_Q_STEP, Codec, Image, make_quant
+
+
+@dataclass
+class Request:
+    kind: str                       # "encode" or "decode"
+    pixels: torch.Tensor | None = None   # encode: host uint8 [H, W] (pinned is fastest)
+    handle: int | None = None       # decode: store handle
+    t_arrival: float = 0.0
+    t_admit: float = 0.0
+    t_done: float = 0.0
+    result: object = None           # encode: handle; decode: host uint8 [H, W]
+    error: str | None = None
+    done: threading.Event = field(default_factory=threading.Event)
+    # internal
+    _need: int = 0
+    _dev: list = field(default_factory=list)
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.t_arrival
+
+
+class CoefStore:
+    """Quantised coefficients kept on the device, keyed by handle, oldest first."""
+
+    def __init__(self):
+        self.entries: collections.OrderedDict[int, dict] = collections.OrderedDict()
+        self.bytes = 0
+
+    def put(self, handle, coef, height, width):
+        self.entries[handle] = {"coef": coef, "h": height, "w": width, "refs": 0}
+        self.bytes += coef.numel() * 2
+
+    def get(self, handle):
+        return self.entries.get(handle)
+
+    def evictable(self):
+        return [h for h, e in self.entries.items() if e["refs"] == 0]
+
+    def evict(self, handle) -> int:
+        e = self.entries.pop(handle)
+        nbytes = e["coef"].numel() * 2
+        self.bytes -= nbytes
+        return nbytes
+
+
+class Server:
+    def __init__(self, device: int = 0, budget_bytes: int = 4 << 30, streams: int = 4, quant=None,
+                 codec: Codec | None = None, max_batch: int = 256):
+        self.device = device
+        self.dev = torch.device("cuda", device)
+        self.codec = codec or Codec(device)
+        self.budget = int(budget_bytes)
+        self.quant = quant if quant is not None else make_quant(ADCT_Q_STEP, _default_table())
+        self.streams = [torch.cuda.Stream(self.dev) for _ in range(streams)]
+        self._stream_rr = itertools.cycle(range(streams))
+        self.max_batch = max_batch
+        self.store = CoefStore()
+        self.in_flight_bytes = 0
+        self._arrivals: collections.deque[Request] = collections.deque()
+        self._queue: collections.deque[Request] = collections.deque()
+        self._batches: list[tuple[torch.cuda.Event, list[Request]]] = []
+        self._handles = itertools.count(1)
+        self._lock = threading.Lock()
+        self._wake = threading.Event()
+        self._stop = False
+        self.stats = {"launches": 0, "admitted": 0, "rejected": 0, "evicted": 0, "max_overlap": 0}
+        self._thread = threading.Thread(target=self._loop, name="adct-server", daemon=True)
+        self._thread.start()
+
+    # -- client side -----------------------------------------------------
+    def submit(self, req: Request) -> Request:
+        if not req.t_arrival:
+            req.t_arrival = time.perf_counter()
+        with self._lock:
+            self._arrivals.append(req)
+        self._wake.set()
+        return req
+
+    def encode(self, pixels: torch.Tensor) -> Request:
+        return self.submit(Request("encode", pixels=pixels))
+
+    def decode(self, handle: int) -> Request:
+        return self.submit(Request("decode", handle=handle))
+
+    def drain(self, timeout: float = 60.0) -> None:
+        t_end = time.perf_counter() + timeout
+        while time.perf_counter() < t_end:
+            with self._lock:
+                busy = bool(self._arrivals or self._queue or self._batches)
+            if not busy:
+                return
+            time.sleep(0.0005)
+        raise TimeoutError("server did not drain")
+
+    def close(self):
+        self._stop = True
+        self._wake.set()
+        self._thread.join()
+
+    # -- scheduler -------------------------------------------------------
+    def _need_bytes(self, r: Request) -> int:
+        if r.kind == "encode":
+            H, W = r.pixels.shape
+            return 3 * H * W  # pixels + int16 coefficients
+        e = self.store.get(r.handle)
+        return 0 if e is None else e["h"] * e["w"]  # output pixels
+
+    def _retire(self):
+        still = []
+        for ev, reqs in self._batches:
+            if ev.query():
+                now = time.perf_counter()
+                for r in reqs:
+                    if r.kind == "encode":
+                        coef = r._dev[1]
+                        H, W = r.pixels.shape
+                        self.store.put(r.result, coef, H, W)
+                        self.in_flight_bytes -= H * W  # pixel staging freed, coefficients stay in the store
+                    else:
+                        e = self.store.get(r.handle)
+                        e["refs"] -= 1
+                        self.in_flight_bytes -= r._need
+                    r._dev = []
+                    r.t_done = now
+                    r.done.set()
+            else:
+                still.append((ev, reqs))
+        self._batches = still
+
+    def _used(self) -> int:
+        return self.in_flight_bytes + self.store.bytes
+
+    def _admit(self):
+        admitted = []
+        while self._queue and len(admitted) < self.max_batch:
+            r = self._queue[0]
+            if r.kind == "decode" and (self.store.get(r.handle) is None):
+                self._queue.popleft()
+                r.error = "unknown handle"
+                r.t_done = time.perf_counter()
+                self.stats["rejected"] += 1
+                r.done.set()
+                continue
+            need = self._need_bytes(r)
+            if need > self.budget:
+                self._queue.popleft()
+                r.error = "request larger than the device-memory budget"
+                r.t_done = time.perf_counter()
+                self.stats["rejected"] += 1
+                r.done.set()
+                continue
+            while self._used() + need > self.budget:
+                victims = [h for h in self.store.evictable() if not (r.kind == "decode" and h == r.handle)]
+                if not victims:
+                    break
+                self.store.evict(victims[0])
+                self.stats["evicted"] += 1
+            if self._used() + need > self.budget:
+                break  # wait for running batches to free memory
+            self._queue.popleft()
+            r._need = need
+            r.t_admit = time.perf_counter()
+            self.in_flight_bytes += need
+            if r.kind == "decode":
+                self.store.get(r.handle)["refs"] += 1
+            admitted.append(r)
+        return admitted
+
+    def _launch(self, reqs):
+        enc = [r for r in reqs if r.kind == "encode"]
+        dec = [r for r in reqs if r.kind == "decode"]
+        for group, kind in ((enc, "encode"), (dec, "decode")):
+            if not group:
+                continue
+            s = self.streams[next(self._stream_rr)]
+            with torch.cuda.stream(s):
+                imgs = []
+                for r in group:
+                    if kind == "encode":
+                        H, W = r.pixels.shape
+                        px = torch.empty((H, W), dtype=torch.uint8, device=self.dev)
+                        px.copy_(r.pixels, non_blocking=True)
+                        coef = torch.empty((1, H // 8, W // 8, 8, 8), dtype=torch.int16, device=self.dev)
+                        r._dev = [px, coef]
+                        r.result = next(self._handles)
+                        imgs.append(Image(px, None, coef))
+                    else:
+                        e = self.store.get(r.handle)
+                        out = torch.empty((e["h"], e["w"]), dtype=torch.uint8, device=self.dev)
+                        r._dev = [out]
+                        imgs.append(Image(None, out, e["coef"]))
+                if kind == "encode":
+                    self.codec.roundtrip(imgs, self.quant, stream=s)
+                else:
+                    self.codec.inverse(imgs, self.quant, stream=s)
+                    for r in group:
+                        host = torch.empty(r._dev[0].shape, dtype=torch.uint8, pin_memory=True)
+                        host.copy_(r._dev[0], non_blocking=True)
+                        r.result = host
+                ev = torch.cuda.Event()
+                ev.record(s)
+            self._batches.append((ev, group))
+            self.stats["launches"] += 1
+        self.stats["max_overlap"] = max(self.stats["max_overlap"], len(self._batches))
+
+    def _loop(self):
+        torch.cuda.set_device(self.dev)
+        while not self._stop:
+            with self._lock:
+                while self._arrivals:
+                    self._queue.append(self._arrivals.popleft())
+            self._retire()
+            admitted = self._admit()
+            if admitted:
+                self.stats["admitted"] += len(admitted)
+                self._launch(admitted)
+            if not admitted:
+                if self._batches or self._queue:
+                    time.sleep(0.00002)
+                else:
+                    self._wake.wait(0.001)
+                    self._wake.clear()
+        # finish outstanding work
+        for ev, _ in self._batches:
+            ev.synchronize()
+        self._retire()
+
+
+def _default_table():
+    import numpy as np
+    i = np.arange(8)[:, None]
+    j = np.arange(8)[None, :]
+    return (1 + np.floor(4 * (1 + i + j))).astype(np.uint16)
+
+
+def poisson_run(server: Server, rate: float, n_requests: int, sizes, images_by_size, seed: int = 0,
+                warm_handles: int = 0):
+    """Drive the server with a Poisson stream of n_requests (50/50 encode and
+    decode; decodes pick a live handle).  Returns the finished requests."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    live = []
+    # warm-up encodes so decodes have handles
+    warm = [server.encode(images_by_size[sizes[k % len(sizes)]][0]) for k in range(warm_handles)]
+    for r in warm:
+        r.done.wait(60)
+        if r.error is None:
+            live.append(r.result)
+    gaps = rng.exponential(1.0 / rate, n_requests)
+    kinds = rng.random(n_requests) < 0.5
+    picks = rng.integers(0, len(sizes), n_requests)
+    reqs = []
+    t = time.perf_counter()
+    for k in range(n_requests):
+        t += gaps[k]
+        while True:
+            now = time.perf_counter()
+            if now >= t:
+                break
+            time.sleep(min(t - now, 0.0005) if t - now > 0.0002 else 0)
+        if kinds[k] or not live:
+            imgs = images_by_size[sizes[picks[k]]]
+            r = Request("encode", pixels=imgs[k % len(imgs)], t_arrival=t)
+        else:
+            r = Request("decode", handle=live[int(rng.integers(0, len(live)))], t_arrival=t)
+        server.submit(r)
+        reqs.append(r)
+        # handles of finished encodes become decodable
+        if k % 16 == 0:
+            live.extend(x.result for x in reqs[-16:] if x.kind == "encode" and x.done.is_set() and x.error is None)
+            live = [h for h in live if server.store.get(h) is not None][-4096:]
+    for r in reqs:
+        r.done.wait(120)
+    return reqs

@@ -251,13 +251,12 @@ def test_autotune_keeps_results(codec):
     Q = make_quant(ADCT_Q_STEP, inputs.step_table(4))
     before = codec.get_launch()
     best, us = codec.autotune([Image(s, d, None) for s, d in zip(srcs, dsts)], Q, reps=2)
-    assert us > 0 and best["threads_per_cta"] in (64, 128, 256)
+    assert us > 0 and best["threads_per_cta"] in (32, 64, 96, 128)
     codec.roundtrip([Image(s, d, None) for s, d in zip(srcs, dsts)], Q)
     torch.cuda.synchronize()
     for x, d in zip(imgs, dsts):
         assert np.array_equal(d.cpu().numpy(), oracle.roundtrip(x, oracle.MODE_STEP, inputs.step_table(4))[1])
-    codec.set_launch(before["threads_per_cta"], before["ctas_per_sm"], before["blocks_per_thread"],
-                     before["stage_coef"])
+    codec.set_launch(before["threads_per_cta"], before["ctas_per_sm"], before["stage_coef"])
 
 
 def test_host_pipeline_equals_device_path(codec):
