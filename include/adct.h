@@ -54,7 +54,8 @@ typedef enum {
   ADCT_ERR_OOM = 4,         /* workspace allocation failed */
   ADCT_ERR_CUDA = 5,        /* a CUDA call failed; see adct_last_error */
   ADCT_ERR_TIMEOUT = 6,     /* a bounded wait gave up */
-  ADCT_ERR_UNSUPPORTED = 7  /* device is not sm_103 / feature not available */
+  ADCT_ERR_UNSUPPORTED = 7, /* device is not sm_103 / feature not available */
+  ADCT_ERR_TOO_LARGE = 8    /* more planes than adct_roundtrip_noalloc can hold */
 } adct_status;
 
 /* Quantiser modes (adct_quant.mode). */
@@ -234,6 +235,33 @@ adct_status adct_butterfly_host(int32_t* vec8, int64_t count, int32_t inverse, i
  */
 adct_status adct_kernel_timing(adct_context* ctx, int32_t enable);
 adct_status adct_kernel_time(adct_context* ctx, double* total_ms, int64_t* launches);
+
+/*
+ * Round trip that allocates nothing.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc, such as plug-ins that
+ * must stay inside a device-memory pool or budget owned by their host
+ * application, latency-critical loops that cannot afford the implicit device
+ * synchronisation of cudaMalloc/cudaFree, and services that must not meet an
+ * out-of-memory failure after start-up.
+ *
+ * Same arguments and results as adct_roundtrip (bit for bit), but no context:
+ * the per-call plane descriptor table lives in a fixed device array inside the
+ * library, sized for ADCT_NOALLOC_MAX_PLANES planes (a plane is one channel of
+ * one image), about 57 KB that every GPU which loads the library keeps until
+ * the process exits.  A batch with more planes returns ADCT_ERR_TOO_LARGE and
+ * launches nothing.  It runs on the calling thread's current CUDA device; the
+ * first call on a device looks up that array's device address, so make the
+ * first call before any stream capture.  The table is copied from host memory
+ * on `stream` (a copy from pageable memory, so the call waits for the work
+ * already queued on that stream).  Every call shares the one array and it
+ * keeps the last call's table; nothing in it needs clearing, because each call
+ * writes the whole table it reads.  Calls whose work overlaps on the GPU (on
+ * different streams, or from different host threads) race on the array:
+ * serialise them on one stream.  Argument errors return the same codes as
+ * adct_roundtrip (there is no context, so no adct_last_error message).
+ */
+#define ADCT_NOALLOC_MAX_PLANES 1024
+adct_status adct_roundtrip_noalloc(const adct_image* imgs, int32_t n, const adct_quant* quant, adct_stream_t stream);
 
 /* Human-readable name of a status code (static string). */
 const char* adct_status_string(adct_status status);

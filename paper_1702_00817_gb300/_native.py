@@ -19,6 +19,8 @@ ADCT_ERR_OOM = 4
 ADCT_ERR_CUDA = 5
 ADCT_ERR_TIMEOUT = 6
 ADCT_ERR_UNSUPPORTED = 7
+ADCT_ERR_TOO_LARGE = 8
+NOALLOC_MAX_PLANES = 1024
 
 ADCT_Q_NONE, ADCT_Q_STEP, ADCT_Q_ZONAL, ADCT_Q_STEP_ZONAL = 0, 1, 2, 3
 
@@ -27,7 +29,7 @@ EXPORTS = (
     "adct_create", "adct_destroy", "adct_forward", "adct_quantise", "adct_inverse", "adct_roundtrip",
     "adct_forward_f32", "adct_backward_f32", "adct_set_launch", "adct_get_launch", "adct_roundtrip_graph",
     "adct_autotune", "adct_roundtrip_host", "adct_butterfly_host", "adct_kernel_timing", "adct_kernel_time",
-    "adct_status_string", "adct_last_error",
+    "adct_roundtrip_noalloc", "adct_status_string", "adct_last_error",
 )
 
 
@@ -101,6 +103,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "adct_butterfly_host": ([P, i64, i32, ctypes.POINTER(i32)], i32),
         "adct_kernel_timing": ([P, i32], i32),
         "adct_kernel_time": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], i32),
+        "adct_roundtrip_noalloc": ([I, i32, Qp, P], i32),
         "adct_status_string": ([i32], ctypes.c_char_p),
         "adct_last_error": ([P], ctypes.c_char_p),
     }

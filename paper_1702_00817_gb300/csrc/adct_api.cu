@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -385,6 +386,7 @@ const char* adct_status_string(adct_status s) {
     case ADCT_ERR_CUDA: return "ADCT_ERR_CUDA";
     case ADCT_ERR_TIMEOUT: return "ADCT_ERR_TIMEOUT";
     case ADCT_ERR_UNSUPPORTED: return "ADCT_ERR_UNSUPPORTED";
+    case ADCT_ERR_TOO_LARGE: return "ADCT_ERR_TOO_LARGE";
   }
   return "ADCT_ERR_UNKNOWN";
 }
@@ -831,6 +833,151 @@ extern "C" adct_status adct_butterfly_host(int32_t* vec8, int64_t count, int32_t
       per = g_adds;
     }
     *adds = (int32_t)per;
+  }
+  return ADCT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// adct_roundtrip_noalloc: the round trip for callers that cannot allocate.
+// The descriptor table that adct_roundtrip keeps in a context workspace lives
+// here in a fixed device array instead; the kernel is the same.
+namespace {
+
+constexpr int kNoAllocPlanes = ADCT_NOALLOC_MAX_PLANES;
+constexpr size_t kNoAllocTable = kNoAllocPlanes * sizeof(PlaneDesc);
+constexpr size_t kNoAllocBytes = kNoAllocTable + (kNoAllocPlanes + 1) * sizeof(int64_t);
+
+// Held by every device that loads the library, until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Host-side view of g_noalloc_scratch: its device address and the SM count,
+// looked up once per device (with that device current).  The symbol's name in
+// host code is only a stand-in; the kernel must get the looked-up address.
+constexpr int kNoAllocMaxDevices = 64;
+struct NoAllocDevice {
+  bool ready = false;
+  void* scratch = nullptr;
+  int sm_count = 0;
+};
+NoAllocDevice g_noalloc_devices[kNoAllocMaxDevices];
+std::mutex g_noalloc_mutex;
+
+adct_status noalloc_device(int dev, void** scratch, int* sm_count) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return ADCT_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  NoAllocDevice& d = g_noalloc_devices[dev];
+  if (!d.ready) {
+    int major = 0, minor = 0, sms = 0;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return ADCT_ERR_CUDA;
+    }
+    if (major != 10 || minor != 3) return ADCT_ERR_UNSUPPORTED;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return ADCT_ERR_CUDA;
+    }
+    d.scratch = p;
+    d.sm_count = sms;
+    d.ready = true;
+  }
+  *scratch = d.scratch;
+  *sm_count = d.sm_count;
+  return ADCT_OK;
+}
+
+bool noalloc_bad_image(const adct_image& im, bool need_coef, bool need_dst) {
+  if (im.width <= 0 || im.height <= 0 || im.width % 8 || im.height % 8 || im.width > 65536 || im.height > 65536)
+    return true;
+  if (im.channels < 1 || im.reserved != 0 || im.pitch < im.width) return true;
+  if (im.channels > 1 && im.plane_stride < im.pitch * im.height) return true;
+  if (!im.src || (need_coef && !im.coef) || (need_dst && !im.dst)) return true;
+  return false;
+}
+
+}  // namespace
+
+extern "C" adct_status adct_roundtrip_noalloc(const adct_image* imgs, int32_t n, const adct_quant* quant,
+                                              adct_stream_t stream) {
+  if (n < 0 || (n > 0 && !imgs) || !quant) return ADCT_ERR_INVALID_ARG;
+  if (n == 0) return ADCT_OK;
+  const bool want_coef = imgs[0].coef != nullptr, want_dst = imgs[0].dst != nullptr;
+  if (!want_coef && !want_dst) return ADCT_ERR_INVALID_ARG;
+  CodecLaunch cl{};
+  cl.kind = (want_coef && want_dst) ? K_RT_FULL : (want_dst ? K_RT_PIX : K_RT_COEF);
+  adct_status st = build_quant(nullptr, quant, true, cl.qp, cl.evenq);
+  if (st != ADCT_OK) return st;
+  cl.qmode = quant->mode;
+
+  // Descriptor table built on the stack: nothing is allocated.
+  struct {
+    PlaneDesc planes[kNoAllocPlanes];
+    int64_t starts[kNoAllocPlanes + 1];
+  } table;
+  static_assert(sizeof(table) == kNoAllocBytes, "table layout matches the device array");
+  int32_t np = 0;
+  int64_t total = 0;
+  for (int32_t m = 0; m < n; ++m) {
+    const adct_image& im = imgs[m];
+    if ((im.coef != nullptr) != want_coef || (im.dst != nullptr) != want_dst) return ADCT_ERR_INVALID_ARG;
+    if (noalloc_bad_image(im, want_coef, want_dst)) {
+      const bool shape = im.width <= 0 || im.height <= 0 || im.width % 8 || im.height % 8 || im.width > 65536 ||
+                         im.height > 65536 || im.pitch < im.width ||
+                         (im.channels > 1 && im.plane_stride < im.pitch * im.height);
+      return shape ? ADCT_ERR_SHAPE : ADCT_ERR_INVALID_ARG;
+    }
+    if ((uintptr_t)im.src % 8 || (uintptr_t)im.dst % 8 || im.pitch % 8 || (im.channels > 1 && im.plane_stride % 8) ||
+        (uintptr_t)im.coef % 16)
+      return ADCT_ERR_ALIGN;
+    if (np + im.channels > kNoAllocPlanes) return ADCT_ERR_TOO_LARGE;
+    const int32_t wb = im.width / 8, hb = im.height / 8;
+    const int64_t nb = (int64_t)wb * hb;
+    for (int32_t c = 0; c < im.channels; ++c) {
+      PlaneDesc& d = table.planes[np];
+      d.src = im.src + (int64_t)c * im.plane_stride;
+      d.dst = im.dst ? im.dst + (int64_t)c * im.plane_stride : nullptr;
+      d.coef = im.coef ? im.coef + (int64_t)c * nb * 64 : nullptr;
+      d.pitch = im.pitch;
+      d.first = total;
+      d.wb = wb;
+      d.hb = hb;
+      table.starts[np] = total;
+      ++np;
+      total += nb;
+    }
+  }
+  table.starts[np] = total;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return ADCT_ERR_CUDA;
+  }
+  void* scratch = nullptr;
+  int sm_count = 0;
+  st = noalloc_device(dev, &scratch, &sm_count);
+  if (st != ADCT_OK) return st;
+  // planes at offset 0, starts right after the planes of this call
+  const size_t plane_bytes = (size_t)np * sizeof(PlaneDesc);
+  const size_t start_bytes = (size_t)(np + 1) * sizeof(int64_t);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(scratch, table.planes, plane_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync((char*)scratch + plane_bytes, table.starts, start_bytes, cudaMemcpyHostToDevice, s) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return ADCT_ERR_CUDA;
+  }
+  cl.planes = (const PlaneDesc*)scratch;
+  cl.starts = (const int64_t*)((char*)scratch + plane_bytes);
+  cl.nplanes = np;
+  cl.total = total;
+  const LaunchShape shape{128, 3, 1};
+  if (launch_codec(cl, shape, sm_count, s) != cudaSuccess) {
+    cudaGetLastError();
+    return ADCT_ERR_CUDA;
   }
   return ADCT_OK;
 }
