@@ -41,7 +41,7 @@ def parse():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["roundtrip"], default="roundtrip")
+    p.add_argument("--workload", choices=["roundtrip", "ragged", "float", "serving"], default="roundtrip")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--images", type=int, default=N_IMG)
@@ -404,11 +404,214 @@ def run_roundtrip(args):
     return 0
 
 
+def _event_time(fn, steps, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(steps):
+        fn(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1000.0
+
+
+def run_ragged(args):
+    """Ragged batch (1000 three-channel images, sides log-uniform over 64..4096):
+    one graph-captured launch vs the same launch eager vs one launch per image."""
+    import torch
+
+    from paper_1702_00817_gb300 import _build, inputs
+    from paper_1702_00817_gb300.codec import ADCT_Q_STEP, Codec, Image, image_array, make_quant
+    d = Dist()
+    dev = torch.device("cuda", d.local)
+    torch.cuda.set_device(dev)
+    if d.rank == 0 or not _build.up_to_date():
+        _build.build()
+    d.barrier()
+    n = 1000
+    sizes = inputs.ragged_sizes(n, seed=inputs.BASE_SEED + d.rank)
+    srcs = [inputs.synth_image_device(h, w, inputs.BASE_SEED + d.rank * n + k, 3, dev) for k, (h, w) in enumerate(sizes)]
+    dsts = [torch.empty_like(x) for x in srcs]
+    coefs = [torch.empty((3, h // 8, w // 8, 8, 8), dtype=torch.int16, device=dev) for (h, w) in sizes]
+    images = [Image(s_, d_, c_) for s_, d_, c_ in zip(srcs, dsts, coefs)]
+    blocks = sum(3 * (h // 8) * (w // 8) for h, w in sizes)
+    q = make_quant(ADCT_Q_STEP, inputs.step_table(4))
+    codec = Codec(d.local)
+    stream = torch.cuda.current_stream(dev)
+    sh = ctypes.c_void_p(stream.cuda_stream)
+    arr = image_array(images)
+    singles = [image_array([im]) for im in images]
+    lib, ctx = codec.lib, codec.ctx
+    rep = ctypes.c_int32()
+
+    def graph(i):
+        assert lib.adct_roundtrip_graph(ctx, arr, n, ctypes.byref(q), sh, ctypes.byref(rep)) == 0
+
+    def eager(i):
+        assert lib.adct_roundtrip(ctx, arr, n, ctypes.byref(q), sh) == 0
+
+    def loop(i):
+        for a in singles:
+            assert lib.adct_roundtrip(ctx, a, 1, ctypes.byref(q), sh) == 0
+
+    best, best_us = codec.autotune(images, q, reps=3)
+    for fn in (graph, eager, loop):
+        for i in range(max(3, args.warmup)):
+            fn(i)
+    steps = max(1, min(args.steps, 50))
+    codec.kernel_time()
+    codec.kernel_timing(True)
+    d.barrier()
+    t_graph = d.max(_event_time(graph, steps, stream))
+    kernel_ms, launches = codec.kernel_time()
+    t_eager = d.max(_event_time(eager, steps, stream))
+    t_loop = d.max(_event_time(loop, steps, stream))
+    codec.kernel_timing(False)
+    # outputs of the three forms must agree bit for bit on a sample
+    out_graph = [dsts[k].clone() for k in (0, n // 2, n - 1)]
+    eager(0)
+    torch.cuda.synchronize()
+    same = all(torch.equal(a, dsts[k]) for a, k in zip(out_graph, (0, n // 2, n - 1)))
+    peak, peak_kind = measured_peaks()
+    total = d.sum(blocks * steps)
+    value = total / t_graph
+    if d.rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": d.ws, "steps": steps,
+                "warmup": max(3, args.warmup), "ms_per_step": 1000 * t_graph / steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": f"ragged batch {n} x 3-channel u8, sides 8*round(2^U[6,12]/8), step s=4, "
+                                       f"one graph-captured launch per step", "blocks_per_gpu": blocks,
+                           "l2": "inputs larger than L2", "autotuned_launch": best, "autotune_us": best_us},
+                "forms": {"graph_one_launch_blocks_s": value, "eager_one_launch_blocks_s": total / t_eager,
+                          "per_image_loop_blocks_s": total / t_loop, "graph_vs_loop": t_loop / t_graph,
+                          "outputs_identical": bool(same)},
+                "gbs": value * BYTES_PER_BLOCK / 1e9, "hbm_frac": value * BYTES_PER_BLOCK / 1e9 / peak,
+                "roofline": {"bound": "hbm", "achieved": blocks * BYTES_PER_BLOCK / (kernel_ms / max(1, launches) / 1e3) / 1e9,
+                             "peak": peak, "unit": "GB/s", "peak_kind": peak_kind,
+                             "frac": blocks * BYTES_PER_BLOCK / (kernel_ms / max(1, launches) / 1e3) / 1e9 / peak,
+                             "kernel": "graph (descriptor upload + k_codec<RT_FULL>)", "traffic": None},
+                "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
+    codec.close()
+    d.close()
+    return 0
+
+
+def run_float(args):
+    """Float32 forward (D T x T^T D + soft quantiser) and adjoint on 64 x 3 x 512 x 512."""
+    import numpy as np
+    import torch
+
+    from paper_1702_00817_gb300 import _build, inputs
+    from paper_1702_00817_gb300.codec import Codec
+    d = Dist()
+    dev = torch.device("cuda", d.local)
+    torch.cuda.set_device(dev)
+    if d.rank == 0 or not _build.up_to_date():
+        _build.build()
+    d.barrier()
+    x = torch.from_numpy(inputs.normal_batch((64, 3, 512, 512), seed=inputs.BASE_SEED + d.rank)).to(dev)
+    gy = torch.from_numpy(inputs.normal_batch((64, 3, 512, 512), seed=inputs.BASE_SEED + 1 + d.rank)).to(dev)
+    y = torch.empty_like(x)
+    gx = torch.empty_like(x)
+    Q = np.ones(64)
+    codec = Codec(d.local)
+    blocks = x.numel() // 64
+
+    def step(i):
+        codec.forward_f32(x, Q, out=y)
+        codec.backward_f32(x, gy, Q, out=gx)
+
+    for i in range(max(3, args.warmup)):
+        step(i)
+    stream = torch.cuda.current_stream(dev)
+    codec.kernel_time()
+    codec.kernel_timing(True)
+    d.barrier()
+    t = d.max(_event_time(step, args.steps, stream))
+    kernel_ms, launches = codec.kernel_time()
+    codec.kernel_timing(False)
+    peak, peak_kind = measured_peaks()
+    total = d.sum(blocks * args.steps)
+    value = total / t
+    if d.rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": d.ws, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": 1000 * t / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic N(0,1)",
+                "config": {"workload": "float32 64x3x512x512: forward D T x T^T D + soft quantiser (Q=1), "
+                                       "then the adjoint kernel", "l2": "inputs larger than L2 (201 MB each)"},
+                "gbs": value * (512 + 768) / 1e9, "hbm_frac": value * (512 + 768) / 1e9 / peak,
+                "roofline": {"bound": "hbm", "achieved": blocks * (512 + 768) / (kernel_ms / max(1, launches) * 2 / 1e3) / 1e9,
+                             "peak": peak, "unit": "GB/s", "peak_kind": peak_kind,
+                             "frac": blocks * (512 + 768) / (kernel_ms / max(1, launches) * 2 / 1e3) / 1e9 / peak,
+                             "kernel": "k_float_fwd + k_float_bwd (mean of the pair)", "traffic": None},
+                "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
+    codec.close()
+    d.close()
+    return 0
+
+
+def run_serving(args):
+    """Poisson stream of encode/decode requests (50/50) of sizes uniform over
+    {256^2, 512^2, 1080x1920, 2160x3840, 4096^2}, 4 GB device budget."""
+    import numpy as np
+    import torch
+
+    from paper_1702_00817_gb300 import _build, inputs
+    from paper_1702_00817_gb300.serve import Server, poisson_run
+    d = Dist()
+    dev = torch.device("cuda", d.local)
+    torch.cuda.set_device(dev)
+    if d.rank == 0 or not _build.up_to_date():
+        _build.build()
+    d.barrier()
+    sizes = [(256, 256), (512, 512), (1080, 1920), (2160, 3840), (4096, 4096)]
+    imgs = {hw: [inputs.synth_image_device(hw[0], hw[1], 7000 + 10 * i + k, 1, dev)[0].cpu().pin_memory()
+                 for k in range(2)] for i, hw in enumerate(sizes)}
+    srv = Server(d.local, budget_bytes=4 << 30, streams=4)
+    poisson_run(srv, rate=500.0, n_requests=100, sizes=sizes, images_by_size=imgs, seed=1, warm_handles=20)
+    rows = []
+    duration = 1.5
+    for rate in (100, 500, 1000, 2000, 5000):
+        n_req = max(20, int(rate * duration))
+        t0 = time.perf_counter()
+        reqs = poisson_run(srv, rate=float(rate), n_requests=n_req, sizes=sizes, images_by_size=imgs, seed=rate)
+        wall = max(r.t_done for r in reqs) - t0
+        ok = [r for r in reqs if r.error is None]
+        lat = np.array([r.latency for r in ok]) * 1000.0
+        px = sum(r.pixels.numel() if r.kind == "encode" else srv_size(srv, r) for r in ok)
+        rows.append({"offered_req_s": rate, "req_s": len(ok) / wall, "p50_ms": float(np.percentile(lat, 50)),
+                     "p99_ms": float(np.percentile(lat, 99)), "errors": len(reqs) - len(ok),
+                     "blocks_s": px / 64 / wall})
+    stats = dict(srv.stats)
+    srv.close()
+    if d.rank == 0:
+        top = rows[-1]
+        line = {"metric": METRIC, "value": top["req_s"], "unit": "req/s", "n_gpus": d.ws, "steps": len(rows),
+                "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int32", "data": "synthetic",
+                "config": {"workload": "serving: Poisson encode/decode 50/50, sizes {256^2,512^2,1080x1920,"
+                                       "2160x3840,4096^2}, 4 GB budget, on-device coefficient store",
+                           "seconds_per_rate": duration},
+                "serving": rows, "p50_ms": top["p50_ms"], "p99_ms": top["p99_ms"], "server_stats": stats}
+        print(json.dumps(line), flush=True)
+    d.close()
+    return 0
+
+
+def srv_size(srv, r):
+    return r.result.numel() if r.result is not None and hasattr(r.result, "numel") else 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    return run_roundtrip(args)
+    return {"roundtrip": run_roundtrip, "ragged": run_ragged, "float": run_float,
+            "serving": run_serving}[args.workload](args)
 
 
 if __name__ == "__main__":

@@ -46,6 +46,33 @@ def synth_image(height: int, width: int, seed: int, channels: int = 1) -> np.nda
     return np.stack([_cosine_plane(rng, height, width) for _ in range(channels)])
 
 
+def synth_image_device(height: int, width: int, seed: int, channels: int = 1, device="cuda"):
+    """Same recipe evaluated on a CUDA device in float32 (for large benchmark
+    batches): the per-image parameters come from the same numpy stream as
+    synth_image; the noise comes from a torch generator seeded with `seed`.
+    Returns a uint8 tensor [channels, height, width] on `device`."""
+    import torch
+    rng = np.random.default_rng(seed)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    ys = torch.arange(height, device=device, dtype=torch.float32)[:, None]
+    xs = torch.arange(width, device=device, dtype=torch.float32)[:, None]
+    out = torch.empty((channels, height, width), dtype=torch.uint8, device=device)
+    for c in range(channels):
+        amp = torch.tensor(rng.uniform(4.0, 24.0, 8), dtype=torch.float32, device=device)
+        fx = torch.tensor(rng.integers(0, 9, 8), dtype=torch.float32, device=device)
+        fy = torch.tensor(rng.integers(0, 9, 8), dtype=torch.float32, device=device)
+        phi = torch.tensor(rng.uniform(0.0, 2.0 * math.pi, 8), dtype=torch.float32, device=device)
+        a = 2.0 * math.pi * fy[None, :] * ys / height + phi[None, :]
+        b = 2.0 * math.pi * fx[None, :] * xs / width
+        left = torch.cat([torch.cos(a) * amp, -torch.sin(a) * amp], dim=1)
+        right = torch.cat([torch.cos(b), torch.sin(b)], dim=1)
+        smooth = 128.0 + left @ right.T
+        noise = torch.randint(-16, 17, (height, width), generator=gen, device=device, dtype=torch.int16)
+        out[c] = (torch.round(smooth) + noise).clamp_(0, 255).to(torch.uint8)
+    return out
+
+
 def synth_batch(n: int, height: int, width: int, base_seed: int = BASE_SEED, channels: int = 1,
                 threads: int = 8) -> np.ndarray:
     """A uniform batch, [n, channels, height, width] uint8, image i seeded base_seed + i."""

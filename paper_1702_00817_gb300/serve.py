@@ -145,8 +145,8 @@ class Server:
                     if r.kind == "encode":
                         coef = r._dev[1]
                         H, W = r.pixels.shape
-                        self.store.put(r.result, coef, H, W)
-                        self.in_flight_bytes -= H * W  # pixel staging freed, coefficients stay in the store
+                        self.store.put(r.result, coef, H, W)  # the coefficients now count against the store
+                        self.in_flight_bytes -= r._need
                     else:
                         e = self.store.get(r.handle)
                         e["refs"] -= 1
