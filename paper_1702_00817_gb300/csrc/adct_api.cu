@@ -24,9 +24,12 @@ constexpr int kPipeSlots = 3;   // host pipeline stages in flight
 
 struct Slot {
   void* dev = nullptr;
-  void* host = nullptr;
+  void* host = nullptr;   // pinned staging; after an upload it mirrors the device copy
   size_t cap = 0;
-  cudaEvent_t done = nullptr;
+  size_t bytes = 0;       // size of the table the device copy holds (0: none)
+  cudaEvent_t done = nullptr;      // last kernel that read the slot
+  cudaEvent_t uploaded = nullptr;  // the upload of the current table
+  cudaStream_t stream = nullptr;   // stream of the last kernel that read the slot
   bool pending = false;
 };
 
@@ -235,6 +238,23 @@ void fill_table(void* host, const std::vector<PlaneDesc>& planes, const std::vec
   std::memcpy((char*)host + planes.size() * sizeof(PlaneDesc), starts.data(), starts.size() * sizeof(int64_t));
 }
 
+// Finds a slot whose device copy already holds exactly this table (a batch
+// repeated call after call) and was last read on the same stream: it is reused
+// as is, with no upload.  Only same-stream reuse is allowed, so that the slot's
+// `done` event, recorded after the new kernel, still covers every earlier
+// reader before the slot is ever overwritten.
+Slot* find_cached_slot(adct_context* ctx, const std::vector<PlaneDesc>& planes, const std::vector<int64_t>& starts,
+                       cudaStream_t stream) {
+  const size_t pb = planes.size() * sizeof(PlaneDesc), bytes = pb + starts.size() * sizeof(int64_t);
+  for (Slot& s : ctx->slots) {
+    if (s.bytes != bytes || !s.host || s.stream != stream) continue;
+    if (std::memcmp(s.host, planes.data(), pb) == 0 &&
+        std::memcmp((const char*)s.host + pb, starts.data(), starts.size() * sizeof(int64_t)) == 0)
+      return &s;
+  }
+  return nullptr;
+}
+
 // Takes the next workspace slot, waiting for the work that last used it.
 adct_status acquire_slot(adct_context* ctx, size_t bytes, Slot** out) {
   Slot& s = ctx->slots[ctx->next_slot];
@@ -243,6 +263,7 @@ adct_status acquire_slot(adct_context* ctx, size_t bytes, Slot** out) {
     ADCT_CUDA(ctx, cudaEventSynchronize(s.done));
     s.pending = false;
   }
+  s.bytes = 0;
   if (s.cap < bytes) {
     size_t cap = std::max<size_t>(bytes, 4096);
     cap = (cap + 4095) / 4096 * 4096;
@@ -317,12 +338,16 @@ adct_status run_codec(adct_context* ctx, const adct_image* imgs, int32_t n, cons
   if (cl.total == 0) return ADCT_OK;
   if (kind == K_QUANTISE && quant->mode == ADCT_Q_NONE) return ADCT_OK;  // identity
   DeviceGuard guard(ctx->device);
-  Slot* slot = nullptr;
   const size_t bytes = table_bytes(planes.size());
-  st = acquire_slot(ctx, bytes, &slot);
-  if (st != ADCT_OK) return st;
-  fill_table(slot->host, planes, starts);
-  ADCT_CUDA(ctx, cudaMemcpyAsync(slot->dev, slot->host, bytes, cudaMemcpyHostToDevice, stream));
+  Slot* slot = find_cached_slot(ctx, planes, starts, stream);
+  if (!slot) {
+    st = acquire_slot(ctx, bytes, &slot);
+    if (st != ADCT_OK) return st;
+    fill_table(slot->host, planes, starts);
+    ADCT_CUDA(ctx, cudaMemcpyAsync(slot->dev, slot->host, bytes, cudaMemcpyHostToDevice, stream));
+    ADCT_CUDA(ctx, cudaEventRecord(slot->uploaded, stream));
+    slot->bytes = bytes;
+  }
   cl.planes = (const PlaneDesc*)slot->dev;
   cl.starts = (const int64_t*)((char*)slot->dev + planes.size() * sizeof(PlaneDesc));
   cl.nplanes = (int32_t)planes.size();
@@ -332,6 +357,7 @@ adct_status run_codec(adct_context* ctx, const adct_image* imgs, int32_t n, cons
   if (e != cudaSuccess) return cuda_fail(ctx, e, "codec kernel launch");
   ADCT_CUDA(ctx, cudaEventRecord(slot->done, stream));
   slot->pending = true;
+  slot->stream = stream;
   return ADCT_OK;
 }
 
@@ -409,7 +435,8 @@ adct_status adct_create(adct_context** out, int32_t device) {
   ctx->sm_count = prop.multiProcessorCount;
   DeviceGuard guard(device);
   for (auto& s : ctx->slots) {
-    if (cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess) {
+    if (cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s.uploaded, cudaEventDisableTiming) != cudaSuccess) {
       adct_destroy(ctx);
       return ADCT_ERR_CUDA;
     }
@@ -430,6 +457,7 @@ void adct_destroy(adct_context* ctx) {
       if (s.pending) cudaEventSynchronize(s.done);
       cudaEventDestroy(s.done);
     }
+    if (s.uploaded) cudaEventDestroy(s.uploaded);
     if (s.dev) cudaFree(s.dev);
     if (s.host) cudaFreeHost(s.host);
   }
@@ -750,15 +778,35 @@ adct_status adct_roundtrip_host(adct_context* ctx, const adct_image* himgs, int3
       p.coef_cap = 2 * pix_cap;
     }
   }
+  // 1D copies of contiguous images are merged with their neighbours when both
+  // sides are contiguous, so a batch laid out back to back moves in a few
+  // large copies instead of one per plane.
+  struct Run {
+    char* dst;
+    const char* src;
+    size_t bytes;
+  };
+  auto add_run = [](std::vector<Run>& runs, void* dst, const void* src, size_t bytes) {
+    if (!runs.empty() && runs.back().dst + runs.back().bytes == (char*)dst &&
+        runs.back().src + runs.back().bytes == (const char*)src)
+      runs.back().bytes += bytes;
+    else
+      runs.push_back(Run{(char*)dst, (const char*)src, bytes});
+  };
   std::vector<adct_image> dimgs;
+  std::vector<Run> h2d, d2h_coef, d2h_pix;
   for (size_t c = 0; c + 1 < bounds.size(); ++c) {
     PipeSlot& p = ctx->pipe[c % kPipeSlots];
     cudaStream_t s = p.stream;
     dimgs.clear();
+    h2d.clear();
+    d2h_coef.clear();
+    d2h_pix.clear();
     size_t off = 0;
     for (int32_t m = bounds[c]; m < bounds[c + 1]; ++m) {
       const adct_image& h = himgs[m];
       const size_t plane = (size_t)h.width * h.height;
+      const bool packed = h.pitch == h.width && (h.channels == 1 || h.plane_stride == (int64_t)plane);
       adct_image d{};
       d.src = p.src + off;
       d.dst = want_dst ? p.dst + off : nullptr;
@@ -768,24 +816,36 @@ adct_status adct_roundtrip_host(adct_context* ctx, const adct_image* himgs, int3
       d.channels = h.channels;
       d.pitch = h.width;
       d.plane_stride = (int64_t)plane;
-      for (int32_t ch = 0; ch < h.channels; ++ch)
-        ADCT_CUDA(ctx, cudaMemcpy2DAsync(p.src + off + ch * plane, h.width, h.src + (int64_t)ch * h.plane_stride, h.pitch,
-                                         h.width, h.height, cudaMemcpyHostToDevice, s));
+      if (packed) {
+        add_run(h2d, p.src + off, h.src, plane * h.channels);
+      } else {
+        for (int32_t ch = 0; ch < h.channels; ++ch)
+          ADCT_CUDA(ctx, cudaMemcpy2DAsync(p.src + off + ch * plane, h.width, h.src + (int64_t)ch * h.plane_stride,
+                                           h.pitch, h.width, h.height, cudaMemcpyHostToDevice, s));
+      }
+      if (want_coef) add_run(d2h_coef, h.coef, d.coef, plane * h.channels * sizeof(int16_t));
+      if (want_dst) {
+        if (packed) add_run(d2h_pix, h.dst, d.dst, plane * h.channels);
+      }
       dimgs.push_back(d);
       off += plane * h.channels;
     }
+    for (const Run& r : h2d) ADCT_CUDA(ctx, cudaMemcpyAsync(r.dst, r.src, r.bytes, cudaMemcpyHostToDevice, s));
     adct_status st = run_codec(ctx, dimgs.data(), (int32_t)dimgs.size(), quant, kind, s, ctx->shape);
     if (st != ADCT_OK) return st;
-    for (size_t k = 0; k < dimgs.size(); ++k) {
-      const adct_image& h = himgs[bounds[c] + (int32_t)k];
-      const adct_image& d = dimgs[k];
-      const size_t plane = (size_t)h.width * h.height;
-      if (want_coef)
-        ADCT_CUDA(ctx, cudaMemcpyAsync(h.coef, d.coef, plane * h.channels * sizeof(int16_t), cudaMemcpyDeviceToHost, s));
-      if (want_dst)
+    for (const Run& r : d2h_coef) ADCT_CUDA(ctx, cudaMemcpyAsync(r.dst, r.src, r.bytes, cudaMemcpyDeviceToHost, s));
+    for (const Run& r : d2h_pix) ADCT_CUDA(ctx, cudaMemcpyAsync(r.dst, r.src, r.bytes, cudaMemcpyDeviceToHost, s));
+    if (want_dst) {
+      for (size_t k = 0; k < dimgs.size(); ++k) {
+        const adct_image& h = himgs[bounds[c] + (int32_t)k];
+        const adct_image& d = dimgs[k];
+        const size_t plane = (size_t)h.width * h.height;
+        const bool packed = h.pitch == h.width && (h.channels == 1 || h.plane_stride == (int64_t)plane);
+        if (packed) continue;
         for (int32_t ch = 0; ch < h.channels; ++ch)
           ADCT_CUDA(ctx, cudaMemcpy2DAsync(h.dst + (int64_t)ch * h.plane_stride, h.pitch, d.dst + ch * plane, h.width,
                                            h.width, h.height, cudaMemcpyDeviceToHost, s));
+      }
     }
   }
   for (auto& p : ctx->pipe) ADCT_CUDA(ctx, cudaStreamSynchronize(p.stream));

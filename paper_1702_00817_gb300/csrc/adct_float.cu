@@ -12,6 +12,8 @@
 namespace adct {
 namespace {
 
+constexpr int kFloatThreads = 128;  // with 3 CTAs per SM: up to 168 registers (sinpif/cospif unrolled 64 times)
+
 // d_i = 2^(-a_i / 2): 1/sqrt8, 1/sqrt2, 1/2 (Sec. 2, matrix D)
 __host__ __device__ constexpr float d_of(int i) {
   return scale_exp(i) == 3 ? 0.35355339059327373f : (scale_exp(i) == 2 ? 0.5f : 0.70710678118654752f);
@@ -43,7 +45,7 @@ __device__ __forceinline__ int64_t block_offset(int64_t g, int64_t nb, int32_t w
 }
 
 template <bool SOFT>
-__global__ void __launch_bounds__(256) k_float_fwd(const float* __restrict__ x, float* __restrict__ y, int64_t total,
+__global__ void __launch_bounds__(kFloatThreads, 3) k_float_fwd(const float* __restrict__ x, float* __restrict__ y, int64_t total,
                                                    int64_t nb, int32_t wb, int32_t H, int32_t W, const FloatParams fp) {
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
     const int64_t off = block_offset(g, nb, wb, H, W);
@@ -64,15 +66,14 @@ __global__ void __launch_bounds__(256) k_float_fwd(const float* __restrict__ x, 
 }
 
 template <bool SOFT>
-__global__ void __launch_bounds__(256) k_float_bwd(const float* __restrict__ x, const float* __restrict__ gy,
-                                                   float* __restrict__ gx, int64_t total, int64_t nb, int32_t wb,
-                                                   int32_t H, int32_t W, const FloatParams fp) {
+__global__ void __launch_bounds__(kFloatThreads, 3) k_float_bwd(const float* __restrict__ x, const float* __restrict__ gy,
+                                                      float* __restrict__ gx, int64_t total, int64_t nb, int32_t wb,
+                                                      int32_t H, int32_t W, const FloatParams fp) {
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
     const int64_t off = block_offset(g, nb, wb, H, W);
-    float gv[64];
-    load_block(gy + off, W, gv);
+    // v <- dz/dy * d_i d_j per coefficient (y recomputed from x), then v <- gy * v
+    float v[64];
     if (SOFT) {
-      float v[64];
       load_block(x + off, W, v);
       fwd2d(v);
 #pragma unroll
@@ -80,22 +81,27 @@ __global__ void __launch_bounds__(256) k_float_bwd(const float* __restrict__ x, 
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int k = 8 * i + j;
-          const float t = v[k] * (d_of(i) * d_of(j));
-          gv[k] = gv[k] * (1.0f - cospif(t * fp.r2[k]));
+          const float dd = d_of(i) * d_of(j);
+          v[k] = (1.0f - cospif(v[k] * dd * fp.r2[k])) * dd;
         }
     }
+    const float* gp = gy + off;
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 8; ++i) {
+      const float4 a = __ldcs((const float4*)(gp + (int64_t)i * W));
+      const float4 b = __ldcs((const float4*)(gp + (int64_t)i * W) + 1);
+      const float r[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 #pragma unroll
-      for (int j = 0; j < 8; ++j) gv[8 * i + j] *= d_of(i) * d_of(j);
-    inv2d(gv);
-    store_block(gx + off, W, gv);
+      for (int j = 0; j < 8; ++j) v[8 * i + j] = SOFT ? r[j] * v[8 * i + j] : r[j] * (d_of(i) * d_of(j));
+    }
+    inv2d(v);
+    store_block(gx + off, W, v);
   }
 }
 
 int float_grid(int64_t total, int sm_count) {
-  int64_t want = (total + 255) / 256;
-  const int64_t cap = (int64_t)sm_count * 8;
+  int64_t want = (total + kFloatThreads - 1) / kFloatThreads;
+  const int64_t cap = (int64_t)sm_count * 3;
   if (want > cap) want = cap;
   return (int)(want < 1 ? 1 : want);
 }
@@ -110,8 +116,8 @@ cudaError_t launch_float_forward(const float* x, float* y, int64_t planes, int32
   if (total <= 0) return cudaSuccess;
   FloatParams none{};
   const int grid = float_grid(total, sm_count);
-  if (fp) k_float_fwd<true><<<grid, 256, 0, stream>>>(x, y, total, nb, wb, H, W, *fp);
-  else k_float_fwd<false><<<grid, 256, 0, stream>>>(x, y, total, nb, wb, H, W, none);
+  if (fp) k_float_fwd<true><<<grid, kFloatThreads, 0, stream>>>(x, y, total, nb, wb, H, W, *fp);
+  else k_float_fwd<false><<<grid, kFloatThreads, 0, stream>>>(x, y, total, nb, wb, H, W, none);
   return cudaGetLastError();
 }
 
@@ -123,8 +129,8 @@ cudaError_t launch_float_backward(const float* x, const float* gy, float* gx, in
   if (total <= 0) return cudaSuccess;
   FloatParams none{};
   const int grid = float_grid(total, sm_count);
-  if (fp) k_float_bwd<true><<<grid, 256, 0, stream>>>(x, gy, gx, total, nb, wb, H, W, *fp);
-  else k_float_bwd<false><<<grid, 256, 0, stream>>>(x, gy, gx, total, nb, wb, H, W, none);
+  if (fp) k_float_bwd<true><<<grid, kFloatThreads, 0, stream>>>(x, gy, gx, total, nb, wb, H, W, *fp);
+  else k_float_bwd<false><<<grid, kFloatThreads, 0, stream>>>(x, gy, gx, total, nb, wb, H, W, none);
   return cudaGetLastError();
 }
 

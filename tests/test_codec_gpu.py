@@ -276,6 +276,45 @@ def test_host_pipeline_equals_device_path(codec):
             assert np.array_equal(c.numpy()[k].astype(np.int64), q_ref)
 
 
+def test_repeated_batch_reuses_its_table_and_sees_new_pixels(codec):
+    # the same tensors called again (identical descriptor table, reused without an
+    # upload) must see the new pixel values; a second stream gets its own table
+    Q = inputs.step_table(4)
+    q = make_quant(ADCT_Q_STEP, Q)
+    a = inputs.synth_image(64, 96, 500)[0]
+    b = inputs.synth_image(64, 96, 501)[0]
+    src = _dev_img(a)
+    dst = torch.empty_like(src)
+    coef = _coef_like(src)
+    s2 = torch.cuda.Stream()
+    for k, img in enumerate((a, b, a, b)):
+        src.copy_(torch.from_numpy(img))
+        stream = s2 if k == 3 else torch.cuda.current_stream()
+        stream.wait_stream(torch.cuda.current_stream())
+        codec.roundtrip([Image(src, dst, coef)], q, stream=stream)
+        torch.cuda.current_stream().wait_stream(stream)
+        torch.cuda.synchronize()
+        q_ref, rec_ref = oracle.roundtrip(img, oracle.MODE_STEP, Q)
+        assert np.array_equal(dst.cpu().numpy(), rec_ref)
+        assert np.array_equal(coef.cpu().numpy()[0].astype(np.int64), q_ref)
+
+
+def test_host_pipeline_merges_contiguous_copies(codec):
+    # a contiguous host batch: consecutive images' copies are merged into few large copies
+    n, H, W = 12, 72, 136
+    host = np.ascontiguousarray(inputs.synth_batch(n, H, W, base_seed=300)[:, 0])
+    hs = torch.from_numpy(host).pin_memory()
+    hd = torch.empty_like(hs).pin_memory()
+    hc = torch.empty((n, H // 8, W // 8, 8, 8), dtype=torch.int16).pin_memory()
+    Q = inputs.step_table(16)
+    codec.roundtrip_host([Image(hs[k], hd[k], hc[k:k + 1]) for k in range(n)], make_quant(ADCT_Q_STEP, Q),
+                         chunk_bytes=5 * H * W)
+    for k in (0, 4, 5, 11):
+        q_ref, rec_ref = oracle.roundtrip(host[k], oracle.MODE_STEP, Q)
+        assert np.array_equal(hd[k].numpy(), rec_ref)
+        assert np.array_equal(hc[k].numpy().astype(np.int64), q_ref)
+
+
 @pytest.mark.parametrize("mode,Q,r", [(ADCT_Q_STEP, 4, 64), (ADCT_Q_ZONAL, None, 64)])
 def test_full_size_uniform_batch_sampled(codec, mode, Q, r):
     """256 x 1080x1920 in the launch configuration the benchmark times: sampled
