@@ -112,31 +112,43 @@ __device__ __forceinline__ int16_t* coef_of(const PlaneDesc* d, const Pos& q) {
   return (int16_t*)c + ((int64_t)q.by * __ldg(&d->wb) + q.bx) * 64;
 }
 
-// Plane cursor of one lane: the flat index only grows, so the plane index
-// only moves forward.  Offsets are 32-bit, relative to the warp's chunk start.
+// Plane cursor of one lane: the flat index only grows (by 32 per tile), so the
+// plane index only moves forward and (by, bx) advance incrementally; a
+// division by the plane's width is needed only when a tile crosses a block
+// row.  Offsets are 32-bit, relative to the warp's chunk start.
 struct Cursor {
   int p;
   int32_t first, next_start;  // plane p spans [first, next_start) relative to the chunk start
+  Pos last;                   // position returned by the previous call (plane < 0: none)
 
   __device__ __forceinline__ Pos locate(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts,
                                         int64_t begin, int32_t r, int32_t rend) {
     Pos q;
     if (r >= rend) {
       q.plane = -1; q.by = 0; q.bx = 0;
+      last = q;
       return q;
     }
+    bool moved = false;
     if (r >= next_start) {
       do {
         ++p;
         next_start = (int32_t)min(__ldg(starts + p + 1) - begin, (int64_t)0x7fffffff);
       } while (r >= next_start);
       first = (int32_t)(__ldg(starts + p) - begin);
+      moved = true;
     }
-    const uint32_t f = (uint32_t)(r - first);
     const uint32_t wb = (uint32_t)__ldg(&planes[p].wb);
-    q.plane = p;
-    q.by = f / wb;
-    q.bx = f - q.by * wb;
+    if (!moved && last.plane == p && last.bx + 32 < wb) {  // same block row, 32 blocks further
+      q = last;
+      q.bx += 32;
+    } else {
+      const uint32_t f = (uint32_t)(r - first);
+      q.plane = p;
+      q.by = f / wb;
+      q.bx = f - q.by * wb;
+    }
+    last = q;
     return q;
   }
 };
@@ -168,6 +180,8 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
     cur.p = lo;
     cur.first = (int32_t)(__ldg(starts + lo) - begin);
     cur.next_start = (int32_t)min(__ldg(starts + lo + 1) - begin, (int64_t)0x7fffffff);
+    cur.last.plane = -1;
+    cur.last.by = cur.last.bx = 0;
   }
 
   // Issue the asynchronous input copies of one tile into stage s.
@@ -302,20 +316,25 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
       const int plane0 = __shfl_sync(0xffffffffu, p_cur.plane, 0);
       const unsigned act = __ballot_sync(0xffffffffu, active);
       int16_t* mine = active ? coef_of(d, p_cur) : nullptr;
+      // Instruction k moves bytes [512 k, 512 k + 512) of the tile: lane l takes
+      // 16-byte chunk (l & 7) of block 4 k + (l >> 3), i.e. byte 512 k + 16 l of
+      // the tile; in shared memory that chunk sits at one of two lane-specific
+      // offsets (the swizzle depends on k only through k & 1) plus 512 k.
+      const int pb = lane >> 3, pc = lane & 7;
+      const uint32_t rd0 = pb * 128 + ((pc ^ pb) << 4), rd1 = pb * 128 + ((pc ^ (pb + 4)) << 4);
       if (__all_sync(0xffffffffu, !active || p_cur.plane == plane0)) {
-        int16_t* cbase = (int16_t*)__shfl_sync(0xffffffffu, (unsigned long long)mine, 0);
+        int4* gp = (int4*)__shfl_sync(0xffffffffu, (unsigned long long)mine, 0) + lane;
         const int nact = __popc(act);  // active lanes are a prefix of the warp
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-          const int b = 4 * k + (lane >> 3), c = lane & 7;
-          if (b < nact) __stcs((int4*)(cbase + 64 * b) + c, *(const int4*)(stage_out + swz(b, c)));
+          if (4 * k + pb < nact) __stcs(gp + 32 * k, *(const int4*)(stage_out + 512 * k + ((k & 1) ? rd1 : rd0)));
         }
       } else {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-          const int b = 4 * k + (lane >> 3), c = lane & 7;
+          const int b = 4 * k + pb;
           int16_t* cb = (int16_t*)__shfl_sync(0xffffffffu, (unsigned long long)mine, b);
-          if (cb) __stcs((int4*)cb + c, *(const int4*)(stage_out + swz(b, c)));
+          if (cb) __stcs((int4*)cb + pc, *(const int4*)(stage_out + 512 * k + ((k & 1) ? rd1 : rd0)));
         }
       }
       __syncwarp();
