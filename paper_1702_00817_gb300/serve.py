@@ -42,7 +42,9 @@ class Request:
     error: str | None = None
     done: threading.Event = field(default_factory=threading.Event)
     # internal
+    out_pixels: int = 0             # decode: pixels produced
     _need: int = 0
+    _pinned: bool = False
     _dev: list = field(default_factory=list)
 
     @property
@@ -94,7 +96,8 @@ class Server:
         self._lock = threading.Lock()
         self._wake = threading.Event()
         self._stop = False
-        self.stats = {"launches": 0, "admitted": 0, "rejected": 0, "evicted": 0, "max_overlap": 0}
+        self.stats = {"launches": 0, "admitted": 0, "unknown_handle": 0, "oversized": 0, "evicted": 0,
+                      "max_overlap": 0}
         self._thread = threading.Thread(target=self._loop, name="adct-server", daemon=True)
         self._thread.start()
 
@@ -103,6 +106,13 @@ class Server:
         if not req.t_arrival:
             req.t_arrival = time.perf_counter()
         with self._lock:
+            if req.kind == "decode":
+                # pin the handle while the request waits, so that admission of
+                # other work cannot evict it in between
+                e = self.store.get(req.handle)
+                if e is not None:
+                    e["refs"] += 1
+                    req._pinned = True
             self._arrivals.append(req)
         self._wake.set()
         return req
@@ -112,6 +122,13 @@ class Server:
 
     def decode(self, handle: int) -> Request:
         return self.submit(Request("decode", handle=handle))
+
+    def warm_host_buffers(self, shapes, count: int = 8) -> None:
+        """Pre-fault pinned output buffers of the given [H, W] shapes so that
+        decodes reuse them from torch's pinned-memory cache instead of calling
+        the (slow, synchronising) pinned allocator on the request path."""
+        bufs = [torch.empty(hw, dtype=torch.uint8, pin_memory=True) for hw in shapes for _ in range(count)]
+        del bufs
 
     def drain(self, timeout: float = 60.0) -> None:
         t_end = time.perf_counter() + timeout
@@ -140,6 +157,7 @@ class Server:
         still = []
         for ev, reqs in self._batches:
             if ev.query():
+                self._lock.acquire()
                 now = time.perf_counter()
                 for r in reqs:
                     if r.kind == "encode":
@@ -154,6 +172,7 @@ class Server:
                     r._dev = []
                     r.t_done = now
                     r.done.set()
+                self._lock.release()
             else:
                 still.append((ev, reqs))
         self._batches = still
@@ -162,6 +181,10 @@ class Server:
         return self.in_flight_bytes + self.store.bytes
 
     def _admit(self):
+        with self._lock:
+            return self._admit_locked()
+
+    def _admit_locked(self):
         admitted = []
         while self._queue and len(admitted) < self.max_batch:
             r = self._queue[0]
@@ -169,7 +192,7 @@ class Server:
                 self._queue.popleft()
                 r.error = "unknown handle"
                 r.t_done = time.perf_counter()
-                self.stats["rejected"] += 1
+                self.stats["unknown_handle"] += 1
                 r.done.set()
                 continue
             need = self._need_bytes(r)
@@ -177,7 +200,7 @@ class Server:
                 self._queue.popleft()
                 r.error = "request larger than the device-memory budget"
                 r.t_done = time.perf_counter()
-                self.stats["rejected"] += 1
+                self.stats["oversized"] += 1
                 r.done.set()
                 continue
             while self._used() + need > self.budget:
@@ -192,8 +215,9 @@ class Server:
             r._need = need
             r.t_admit = time.perf_counter()
             self.in_flight_bytes += need
-            if r.kind == "decode":
+            if r.kind == "decode" and not r._pinned:
                 self.store.get(r.handle)["refs"] += 1
+                r._pinned = True
             admitted.append(r)
         return admitted
 
@@ -228,6 +252,7 @@ class Server:
                         host = torch.empty(r._dev[0].shape, dtype=torch.uint8, pin_memory=True)
                         host.copy_(r._dev[0], non_blocking=True)
                         r.result = host
+                        r.out_pixels = host.numel()
                 ev = torch.cuda.Event()
                 ev.record(s)
             self._batches.append((ev, group))
@@ -267,7 +292,9 @@ def _default_table():
 def poisson_run(server: Server, rate: float, n_requests: int, sizes, images_by_size, seed: int = 0,
                 warm_handles: int = 0):
     """Drive the server with a Poisson stream of n_requests (50/50 encode and
-    decode; decodes pick a live handle).  Returns the finished requests."""
+    decode; decodes pick a live handle).  Returns the finished requests; the
+    pixels of finished decodes are released as the stream goes (only their
+    timing is kept), as a client that consumed them would."""
     import numpy as np
     rng = np.random.default_rng(seed)
     live = []
@@ -281,25 +308,38 @@ def poisson_run(server: Server, rate: float, n_requests: int, sizes, images_by_s
     kinds = rng.random(n_requests) < 0.5
     picks = rng.integers(0, len(sizes), n_requests)
     reqs = []
+    pending_enc = []
+    pending_dec = []
     t = time.perf_counter()
     for k in range(n_requests):
         t += gaps[k]
-        while True:
-            now = time.perf_counter()
-            if now >= t:
-                break
-            time.sleep(min(t - now, 0.0005) if t - now > 0.0002 else 0)
+        wait = t - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)  # no busy wait: the arrival time stays t, lateness counts as latency
+        # handles of finished encodes become decodable; decodes pick among the most recent
+        if k % 8 == 0:
+            done = [x for x in pending_enc if x.done.is_set()]
+            pending_enc = [x for x in pending_enc if not x.done.is_set()]
+            live.extend(x.result for x in done if x.error is None)
+            live = live[-64:]
+            still = []
+            for x in pending_dec:
+                if x.done.is_set():
+                    x.result = None
+                else:
+                    still.append(x)
+            pending_dec = still
         if kinds[k] or not live:
             imgs = images_by_size[sizes[picks[k]]]
             r = Request("encode", pixels=imgs[k % len(imgs)], t_arrival=t)
+            pending_enc.append(r)
         else:
             r = Request("decode", handle=live[int(rng.integers(0, len(live)))], t_arrival=t)
+            pending_dec.append(r)
         server.submit(r)
         reqs.append(r)
-        # handles of finished encodes become decodable
-        if k % 16 == 0:
-            live.extend(x.result for x in reqs[-16:] if x.kind == "encode" and x.done.is_set() and x.error is None)
-            live = [h for h in live if server.store.get(h) is not None][-4096:]
     for r in reqs:
         r.done.wait(120)
+        if r.kind == "decode":
+            r.result = None
     return reqs
