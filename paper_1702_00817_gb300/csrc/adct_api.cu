@@ -682,7 +682,7 @@ adct_status adct_autotune(adct_context* ctx, const adct_image* imgs, int32_t n, 
   for (int th : threads_c) {
     for (int cps : ctas_c) {
       if (th * cps > 2048) continue;
-      if ((size_t)cps * codec_smem_bytes(LaunchShape{th, cps, stage}) > 200 * 1024) continue;  // shared memory per SM
+      if ((size_t)cps * codec_smem_bytes(LaunchShape{th, cps, stage}, kind) > 200 * 1024) continue;  // shared memory per SM
       LaunchShape sh{th, cps, stage};
       adct_status st = run_codec(ctx, imgs, n, quant, kind, s, sh);  // warm-up
       if (st != ADCT_OK) { result = st; goto done; }

@@ -38,7 +38,6 @@ namespace adct {
 namespace {
 
 constexpr int kMaxThreads = 128;  // with 3 CTAs per SM: up to 168 registers per thread
-constexpr int kTileBytesIn = 4096;   // one input stage: 32 blocks of coefficients (pixels use 2 KB of it)
 constexpr int kTileBytesOut = 4096;  // output staging: 32 blocks of int16 coefficients
 
 __device__ __forceinline__ int32_t sext_lo16(uint32_t w) { return (int32_t)(int16_t)(w & 0xFFFFu); }
@@ -153,23 +152,165 @@ struct Cursor {
   }
 };
 
+// Blocks per lane per tile: a warp walks its chunk in tiles of 32 * kBpl
+// blocks, lane l owning blocks l, l + 32, ...  One block per lane measured
+// best: two per lane left the instruction count per block unchanged (the
+// overhead is per block, not per tile) and doubled the shared memory per CTA,
+// which ran slower.
+constexpr int kBpl = 1;
+
+// Per-warp shared memory for kind KIND: two input stages and one output stage.
+template <int KIND>
+struct SmemPlan {
+  static constexpr int in_per32 = KindTraits<KIND>::in_pix ? 2048 : 4096;  // one 32-block tile of input
+  static constexpr int in_stage = kBpl * in_per32;
+  static constexpr int out_stage = KindTraits<KIND>::write_coef ? kBpl * kTileBytesOut : 0;
+  static constexpr int warp = 2 * in_stage + out_stage;
+};
+
+// Arithmetic of one 8x8 block: read its input from the input stage, quantise,
+// stage or store q, dequantise, invert and store the pixels.
+template <int KIND, int QMODE, bool EVENQ>
+__device__ __forceinline__ void block_step(const uint8_t* __restrict__ in, uint8_t* __restrict__ stage_out,
+                                           const PlaneDesc* __restrict__ planes, const Pos& pos, int stage_coef,
+                                           const QuantParams& qp, int lane) {
+  using KT = KindTraits<KIND>;
+  if (pos.plane < 0) return;
+  const PlaneDesc* d = planes + pos.plane;
+  int32_t v[64];
+  if (KT::in_pix) {
+    const uint2* st = (const uint2*)in;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const uint2 w = st[i * 32 + lane];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        v[8 * i + j] = (int32_t)__byte_perm(w.x, 0u, 0x4440 | j);
+        v[8 * i + 4 + j] = (int32_t)__byte_perm(w.y, 0u, 0x4440 | j);
+      }
+    }
+    fwd2d(v);  // Z + 8192 e0 e0^T (raw pixels; the level shift lives in the constants)
+  } else {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int4 u = *(const int4*)(in + swz(lane, t));
+      v[8 * t + 0] = sext_lo16(u.x); v[8 * t + 1] = sext_hi16(u.x);
+      v[8 * t + 2] = sext_lo16(u.y); v[8 * t + 3] = sext_hi16(u.y);
+      v[8 * t + 4] = sext_lo16(u.z); v[8 * t + 5] = sext_hi16(u.z);
+      v[8 * t + 6] = sext_lo16(u.w); v[8 * t + 7] = sext_hi16(u.w);
+    }
+  }
+
+  // ---- quantise (q, stored row by row) and dequantise in place (v <- S) ----
+  // S = q * w with w = Q 2^(6 - a_i - a_j) (D^2 merged), plus kDcBias at
+  // (0, 0).  For STEP it is formed from m directly (S = m * w + kw, kw =
+  // -K * w (+ kDcBias)), independent of the q = m - K that goes to memory.
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    int32_t q[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = 8 * i + j;
+      const int32_t bias = (k == 0) ? kDcBias : 0;
+      const int32_t z = v[k];  // raw: Z + 8192 at (0, 0) when the input was pixels
+      // T (X - 128) T^T = T X T^T - 8192 e0 e0^T  (T 1 = 8 e0)
+      const int32_t zoff = (KT::in_pix && k == 0) ? -8192 : 0;
+      if (KIND == K_INVERSE) {
+        q[j] = z;
+        v[k] = (int32_t)((uint32_t)z * (uint32_t)qp.w[k] + (uint32_t)bias);
+      } else if (QMODE == QM_STEP || QMODE == QM_STEP_ZONAL) {
+        int32_t n = z + qp.c[k];
+        if (EVENQ) n += ((z + zoff) >> 31) & qp.sflag[k];
+        const uint32_t m = __umulhi((uint32_t)n, qp.magic[k]);
+        int32_t qq = (int32_t)m - qp.K[k];
+        if (QMODE == QM_STEP_ZONAL) qq &= qp.keep[k];
+        q[j] = qq;
+        if (KT::inv)
+          v[k] = (QMODE == QM_STEP_ZONAL) ? (int32_t)((uint32_t)qq * (uint32_t)qp.w[k] + (uint32_t)bias)
+                                          : (int32_t)(m * (uint32_t)qp.w[k] + (uint32_t)qp.kw[k]);
+      } else {
+        int32_t qq = z + zoff;  // the true coefficient
+        if (QMODE == QM_ZONAL) qq &= qp.keep[k];
+        q[j] = qq;
+        if (KT::inv) v[k] = (int32_t)((uint32_t)qq * (uint32_t)qp.w[k] + (uint32_t)bias);
+      }
+    }
+    if (KT::write_coef) {
+      int4 u;
+      u.x = (int)pack16(q[0], q[1]);
+      u.y = (int)pack16(q[2], q[3]);
+      u.z = (int)pack16(q[4], q[5]);
+      u.w = (int)pack16(q[6], q[7]);
+      if (stage_coef) *(int4*)(stage_out + swz(lane, i)) = u;
+      else __stcs((int4*)coef_of(d, pos) + i, u);
+    }
+  }
+
+  // ---- inverse (8 column, then 8 row transposed butterflies) and output ----
+  if (KT::inv) {
+    inv2d(v);
+    const int64_t pitch = __ldg(&d->pitch);
+    uint8_t* o = dst_of(d) + (int64_t)(8 * pos.by) * pitch + 8 * pos.bx;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      uint2 w;
+      w.x = pixels4(v[8 * i + 0], v[8 * i + 1], v[8 * i + 2], v[8 * i + 3]);
+      w.y = pixels4(v[8 * i + 4], v[8 * i + 5], v[8 * i + 6], v[8 * i + 7]);
+      __stcs((uint2*)(o + i * pitch), w);
+    }
+  }
+}
+
+// Write a staged 32-block half-tile of coefficients back with 512-byte warp
+// stores.  The blocks of a plane are contiguous in coef, so when every active
+// lane is in lane 0's plane the half-tile is one contiguous range.
+__device__ __forceinline__ void write_back(const uint8_t* __restrict__ stage_out, const PlaneDesc* __restrict__ planes,
+                                          const Pos& pos, int lane) {
+  const bool active = pos.plane >= 0;
+  const int plane0 = __shfl_sync(0xffffffffu, pos.plane, 0);
+  const unsigned act = __ballot_sync(0xffffffffu, active);
+  int16_t* mine = active ? coef_of(planes + pos.plane, pos) : nullptr;
+  // Instruction k moves bytes [512 k, 512 k + 512) of the half-tile: lane l
+  // takes 16-byte chunk (l & 7) of block 4 k + (l >> 3), i.e. byte 512 k + 16 l;
+  // in shared memory that chunk sits at one of two lane-specific offsets (the
+  // swizzle depends on k only through k & 1) plus 512 k.
+  const int pb = lane >> 3, pc = lane & 7;
+  const uint32_t rd0 = pb * 128 + ((pc ^ pb) << 4), rd1 = pb * 128 + ((pc ^ (pb + 4)) << 4);
+  if (__all_sync(0xffffffffu, !active || pos.plane == plane0)) {
+    int4* gp = (int4*)__shfl_sync(0xffffffffu, (unsigned long long)mine, 0) + lane;
+    const int nact = __popc(act);  // active lanes are a prefix of the warp
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (4 * k + pb < nact) __stcs(gp + 32 * k, *(const int4*)(stage_out + 512 * k + ((k & 1) ? rd1 : rd0)));
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int b = 4 * k + pb;
+      int16_t* cb = (int16_t*)__shfl_sync(0xffffffffu, (unsigned long long)mine, b);
+      if (cb) __stcs((int4*)cb + pc, *(const int4*)(stage_out + 512 * k + ((k & 1) ? rd1 : rd0)));
+    }
+  }
+}
+
 template <int KIND, int QMODE, bool EVENQ>
 __global__ void __launch_bounds__(kMaxThreads, 3)
 k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts, int32_t nplanes, int64_t total,
         int64_t chunk, int stage_coef, const QuantParams qp) {
   using KT = KindTraits<KIND>;
+  using SP = SmemPlan<KIND>;
+  constexpr int kTile = 32 * kBpl;
   extern __shared__ __align__(128) uint8_t smem[];
   const int lane = threadIdx.x & 31;
-  const int warp_cta = threadIdx.x >> 5;
-  uint8_t* wsm = smem + warp_cta * (2 * kTileBytesIn + kTileBytesOut);
-  uint8_t* stage_out = wsm + 2 * kTileBytesIn;
+  uint8_t* wsm = smem + (threadIdx.x >> 5) * SP::warp;
+  uint8_t* stage_out = wsm + 2 * SP::in_stage;
 
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t begin = gwarp * chunk;
   if (begin >= total) return;  // whole warp exits together
   const int64_t end = min(total, begin + chunk);
-
   const int32_t rend = (int32_t)(end - begin);  // chunk length (< 2^31 blocks)
+
   Cursor cur;
   {
     int lo = 0, hi = nplanes;  // largest p with starts[p] <= begin
@@ -185,161 +326,62 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
   }
 
   // Issue the asynchronous input copies of one tile into stage s.
-  auto issue = [&](int s, const Pos& q) {
-    const uint32_t sa = smem_addr(wsm + s * kTileBytesIn);
-    if (KT::in_pix) {
-      if (q.plane >= 0) {
-        const PlaneDesc* d = planes + q.plane;
-        const int64_t pitch = __ldg(&d->pitch);
-        const uint8_t* src = src_of(d) + (int64_t)(8 * q.by) * pitch + 8 * q.bx;
+  auto issue = [&](int s, const Pos* q) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) cp_async8(sa + (i * 32 + lane) * 8, src + i * pitch);
-      }
-    } else {
-      // Coefficients: lane copies 16-byte chunk c of block b (512 contiguous
-      // bytes per warp instruction when the tile lies in one plane).
-      const int16_t* mine = q.plane >= 0 ? coef_of(planes + q.plane, q) : nullptr;
+    for (int u = 0; u < kBpl; ++u) {
+      const uint32_t sa = smem_addr(wsm + s * SP::in_stage + u * SP::in_per32);
+      if (KT::in_pix) {
+        if (q[u].plane >= 0) {
+          const PlaneDesc* d = planes + q[u].plane;
+          const int64_t pitch = __ldg(&d->pitch);
+          const uint8_t* src = src_of(d) + (int64_t)(8 * q[u].by) * pitch + 8 * q[u].bx;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int b = 4 * k + (lane >> 3), c = lane & 7;
-        const int16_t* cb = (const int16_t*)__shfl_sync(0xffffffffu, (unsigned long long)mine, b);
-        if (cb) cp_async16(sa + swz(b, c), cb + 8 * c);
+          for (int i = 0; i < 8; ++i) cp_async8(sa + (i * 32 + lane) * 8, src + i * pitch);
+        }
+      } else {
+        // Coefficients: lane copies 16-byte chunk c of block b (512 contiguous
+        // bytes per warp instruction when the tile lies in one plane).
+        const int16_t* mine = q[u].plane >= 0 ? coef_of(planes + q[u].plane, q[u]) : nullptr;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int b = 4 * k + (lane >> 3), c = lane & 7;
+          const int16_t* cb = (const int16_t*)__shfl_sync(0xffffffffu, (unsigned long long)mine, b);
+          if (cb) cp_async16(sa + swz(b, c), cb + 8 * c);
+        }
       }
     }
     cp_async_commit();
   };
 
-  Pos p_cur = cur.locate(planes, starts, begin, lane, rend);
-  issue(0, p_cur);
+  Pos pc[kBpl];
+#pragma unroll
+  for (int u = 0; u < kBpl; ++u) pc[u] = cur.locate(planes, starts, begin, 32 * u + lane, rend);
+  issue(0, pc);
   int s = 0;
-  for (int32_t base = 0; base < rend; base += 32, s ^= 1) {
-    const int32_t nbase = base + 32;
+  for (int32_t base = 0; base < rend; base += kTile, s ^= 1) {
+    const int32_t nbase = base + kTile;
     __syncwarp();  // every lane is done reading stage s ^ 1 before it is refilled
-    const Pos p_next = cur.locate(planes, starts, begin, nbase + lane, rend);
-    if (nbase < rend) issue(s ^ 1, p_next);
+    Pos pn[kBpl];
+#pragma unroll
+    for (int u = 0; u < kBpl; ++u) pn[u] = cur.locate(planes, starts, begin, nbase + 32 * u + lane, rend);
+    if (nbase < rend) issue(s ^ 1, pn);
     else cp_async_commit();
     cp_async_wait<1>();
     __syncwarp();
 
-    const bool active = p_cur.plane >= 0;
-    const PlaneDesc* d = planes + (active ? p_cur.plane : 0);
-    int32_t v[64];
-    if (active) {
-      if (KT::in_pix) {
-        const uint2* st = (const uint2*)(wsm + s * kTileBytesIn);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const uint2 w = st[i * 32 + lane];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            v[8 * i + j] = (int32_t)__byte_perm(w.x, 0u, 0x4440 | j);
-            v[8 * i + 4 + j] = (int32_t)__byte_perm(w.y, 0u, 0x4440 | j);
-          }
-        }
-        fwd2d(v);  // Z + 8192 e0 e0^T (raw pixels; the level shift lives in the constants)
-      } else {
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int4 u = *(const int4*)(wsm + s * kTileBytesIn + swz(lane, t));
-          v[8 * t + 0] = sext_lo16(u.x); v[8 * t + 1] = sext_hi16(u.x);
-          v[8 * t + 2] = sext_lo16(u.y); v[8 * t + 3] = sext_hi16(u.y);
-          v[8 * t + 4] = sext_lo16(u.z); v[8 * t + 5] = sext_hi16(u.z);
-          v[8 * t + 6] = sext_lo16(u.w); v[8 * t + 7] = sext_hi16(u.w);
-        }
-      }
-
-      // ---- quantise (q, stored row by row) and dequantise in place (v <- S) ----
-      // S = q * w with w = Q 2^(6 - a_i - a_j) (D^2 merged), plus kDcBias at
-      // (0, 0).  For STEP it is formed from m directly (S = m * w + kw, kw =
-      // -K * w (+ kDcBias)), independent of the q = m - K that goes to memory.
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        int32_t q[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int k = 8 * i + j;
-          const int32_t bias = (k == 0) ? kDcBias : 0;
-          const int32_t z = v[k];  // raw: Z + 8192 at (0, 0) when the input was pixels
-          // T (X - 128) T^T = T X T^T - 8192 e0 e0^T  (T 1 = 8 e0)
-          const int32_t zoff = (KT::in_pix && k == 0) ? -8192 : 0;
-          if (KIND == K_INVERSE) {
-            q[j] = z;
-            v[k] = (int32_t)((uint32_t)z * (uint32_t)qp.w[k] + (uint32_t)bias);
-          } else if (QMODE == QM_STEP || QMODE == QM_STEP_ZONAL) {
-            int32_t n = z + qp.c[k];
-            if (EVENQ) n += ((z + zoff) >> 31) & qp.sflag[k];
-            const uint32_t m = __umulhi((uint32_t)n, qp.magic[k]);
-            int32_t qq = (int32_t)m - qp.K[k];
-            if (QMODE == QM_STEP_ZONAL) qq &= qp.keep[k];
-            q[j] = qq;
-            if (KT::inv)
-              v[k] = (QMODE == QM_STEP_ZONAL) ? (int32_t)((uint32_t)qq * (uint32_t)qp.w[k] + (uint32_t)bias)
-                                              : (int32_t)(m * (uint32_t)qp.w[k] + (uint32_t)qp.kw[k]);
-          } else {
-            int32_t qq = z + zoff;  // the true coefficient
-            if (QMODE == QM_ZONAL) qq &= qp.keep[k];
-            q[j] = qq;
-            if (KT::inv) v[k] = (int32_t)((uint32_t)qq * (uint32_t)qp.w[k] + (uint32_t)bias);
-          }
-        }
-        if (KT::write_coef) {
-          int4 u;
-          u.x = (int)pack16(q[0], q[1]);
-          u.y = (int)pack16(q[2], q[3]);
-          u.z = (int)pack16(q[4], q[5]);
-          u.w = (int)pack16(q[6], q[7]);
-          if (stage_coef) *(int4*)(stage_out + swz(lane, i)) = u;
-          else __stcs((int4*)coef_of(d, p_cur) + i, u);
-        }
-      }
-
-      // ---- inverse (8 column, then 8 row transposed butterflies) and output ----
-      if (KT::inv) {
-        inv2d(v);
-        const int64_t pitch = __ldg(&d->pitch);
-        uint8_t* o = dst_of(d) + (int64_t)(8 * p_cur.by) * pitch + 8 * p_cur.bx;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          uint2 w;
-          w.x = pixels4(v[8 * i + 0], v[8 * i + 1], v[8 * i + 2], v[8 * i + 3]);
-          w.y = pixels4(v[8 * i + 4], v[8 * i + 5], v[8 * i + 6], v[8 * i + 7]);
-          __stcs((uint2*)(o + i * pitch), w);
-        }
-      }
-    }
+    for (int u = 0; u < kBpl; ++u)
+      block_step<KIND, QMODE, EVENQ>(wsm + s * SP::in_stage + u * SP::in_per32, stage_out + u * kTileBytesOut,
+                                     planes, pc[u], stage_coef, qp, lane);
 
     if (KT::write_coef && stage_coef) {
-      // Write the staged tile back with 512-byte warp stores.  The blocks of a
-      // plane are contiguous in coef, so when every active lane is in lane 0's
-      // plane the tile is one contiguous range of 128 bytes per active block.
       __syncwarp();
-      const int plane0 = __shfl_sync(0xffffffffu, p_cur.plane, 0);
-      const unsigned act = __ballot_sync(0xffffffffu, active);
-      int16_t* mine = active ? coef_of(d, p_cur) : nullptr;
-      // Instruction k moves bytes [512 k, 512 k + 512) of the tile: lane l takes
-      // 16-byte chunk (l & 7) of block 4 k + (l >> 3), i.e. byte 512 k + 16 l of
-      // the tile; in shared memory that chunk sits at one of two lane-specific
-      // offsets (the swizzle depends on k only through k & 1) plus 512 k.
-      const int pb = lane >> 3, pc = lane & 7;
-      const uint32_t rd0 = pb * 128 + ((pc ^ pb) << 4), rd1 = pb * 128 + ((pc ^ (pb + 4)) << 4);
-      if (__all_sync(0xffffffffu, !active || p_cur.plane == plane0)) {
-        int4* gp = (int4*)__shfl_sync(0xffffffffu, (unsigned long long)mine, 0) + lane;
-        const int nact = __popc(act);  // active lanes are a prefix of the warp
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          if (4 * k + pb < nact) __stcs(gp + 32 * k, *(const int4*)(stage_out + 512 * k + ((k & 1) ? rd1 : rd0)));
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int b = 4 * k + pb;
-          int16_t* cb = (int16_t*)__shfl_sync(0xffffffffu, (unsigned long long)mine, b);
-          if (cb) __stcs((int4*)cb + pc, *(const int4*)(stage_out + 512 * k + ((k & 1) ? rd1 : rd0)));
-        }
-      }
+      for (int u = 0; u < kBpl; ++u) write_back(stage_out + u * kTileBytesOut, planes, pc[u], lane);
       __syncwarp();
     }
-    p_cur = p_next;
+#pragma unroll
+    for (int u = 0; u < kBpl; ++u) pc[u] = pn[u];
   }
   cp_async_wait<0>();
 }
@@ -381,8 +423,21 @@ KernelFn pick_kernel(int kind, int qmode, bool evenq) {
 
 }  // namespace
 
-size_t codec_smem_bytes(const LaunchShape& shape) {
-  return (size_t)(shape.threads / 32) * (2 * kTileBytesIn + kTileBytesOut);
+namespace {
+int warp_smem(int kind) {
+  switch (kind) {
+    case K_FORWARD: return SmemPlan<K_FORWARD>::warp;
+    case K_QUANTISE: return SmemPlan<K_QUANTISE>::warp;
+    case K_INVERSE: return SmemPlan<K_INVERSE>::warp;
+    case K_RT_FULL: return SmemPlan<K_RT_FULL>::warp;
+    case K_RT_PIX: return SmemPlan<K_RT_PIX>::warp;
+    default: return SmemPlan<K_RT_COEF>::warp;
+  }
+}
+}  // namespace
+
+size_t codec_smem_bytes(const LaunchShape& shape, int kind) {
+  return (size_t)(shape.threads / 32) * warp_smem(kind);
 }
 
 int codec_grid(const LaunchShape& shape, int sm_count, int64_t total) {
@@ -397,7 +452,7 @@ cudaError_t launch_codec(const CodecLaunch& c, const LaunchShape& shape, int sm_
   KernelFn fn = pick_kernel(c.kind, c.qmode, c.evenq);
   if (!fn) return cudaErrorInvalidValue;
   if (shape.threads < 32 || shape.threads > kMaxThreads || shape.threads % 32) return cudaErrorInvalidValue;
-  const size_t smem = codec_smem_bytes(shape);
+  const size_t smem = codec_smem_bytes(shape, c.kind);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -411,7 +466,7 @@ cudaError_t launch_codec(const CodecLaunch& c, const LaunchShape& shape, int sm_
   const int grid = codec_grid(sh, sm_count, c.total);
   const int64_t warps = (int64_t)grid * (shape.threads / 32);
   int64_t chunk = (c.total + warps - 1) / warps;
-  chunk = (chunk + 31) / 32 * 32;
+  chunk = (chunk + 32 * kBpl - 1) / (32 * kBpl) * (32 * kBpl);
   fn<<<grid, shape.threads, smem, stream>>>(c.planes, c.starts, c.nplanes, c.total, chunk, shape.stage_coef, c.qp);
   return cudaGetLastError();
 }

@@ -41,7 +41,7 @@ cudaError_t launch_codec(const CodecLaunch& c, const LaunchShape& shape, int sm_
 
 // Largest grid the persistent kernel uses for this shape (CTAs), and its dynamic shared memory.
 int codec_grid(const LaunchShape& shape, int sm_count, int64_t total);
-size_t codec_smem_bytes(const LaunchShape& shape);
+size_t codec_smem_bytes(const LaunchShape& shape, int kind);
 
 // Float variant (Sec. 2 C^ = D T): forward (optionally soft-quantised) and adjoint.
 struct FloatParams {
