@@ -145,7 +145,10 @@ adct_status adct_quantise(adct_context* ctx, const adct_image* imgs, int32_t n, 
  * Dequantise with D^2 merged (S_ij = q_ij Q_ij 2^(6 - a_i - a_j), Q = 1 for NONE
  * and ZONAL), invert R = T^T S T with the transposed 14-addition flow graph, and
  * reconstruct dst = clamp(floor((R + 32) / 64) + 128, 0, 255) (Sec. 2
- * orthogonality; Sec. 3 "inverse procedure").  Uses coef and dst.
+ * orthogonality; Sec. 3 "inverse procedure").  Uses coef and dst.  coef must
+ * hold quantiser output for this quant, which guarantees |q_ij Q_ij| <= 16384
+ * and keeps the 32-bit arithmetic exact; other values give unspecified (but
+ * memory-safe) pixels.
  */
 adct_status adct_inverse(adct_context* ctx, const adct_image* imgs, int32_t n, const adct_quant* quant,
                          adct_stream_t stream);

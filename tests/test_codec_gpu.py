@@ -144,6 +144,39 @@ def test_split_stages_equal_oracle_and_fused(codec):
     assert np.array_equal(dst.cpu().numpy(), rec_ref)
 
 
+def test_quantise_edges_on_coefficient_input(codec):
+    # quantiser on coefficients given directly: |Z| up to 8192, steps around
+    # the 16384 boundary (a tie at |Z| = 8192, Q = 16384 rounds away from zero)
+    rng = np.random.default_rng(12)
+    edges = np.array([0, 1, -1, 2, -2, 8191, -8191, 8192, -8192, 4096, -4096, 3, -3], np.int64)
+    Z = rng.integers(-8192, 8193, size=(4, 8, 8, 8)).astype(np.int64)
+    Z.reshape(-1)[: edges.size] = edges
+    Z[0, 1, 0, :] = 8192
+    Z[0, 1, 1, :] = -8192
+    for Q in (np.array([1, 2, 3, 4, 16383, 16384, 16385, 65535] * 8, np.uint16),
+              rng.integers(1, 65536, 64).astype(np.uint16), inputs.step_table(1)):
+        for mode in (ADCT_Q_STEP, ADCT_Q_STEP_ZONAL):
+            coef = torch.from_numpy(Z.astype(np.int16).reshape(1, 4, 8, 8, 8)).to(DEV)
+            codec.quantise([Image(None, None, coef)], make_quant(mode, Q, 21))
+            torch.cuda.synchronize()
+            expect = oracle.quantise(Z, MODES[mode], Q, 21)
+            assert np.array_equal(coef.cpu().numpy()[0].astype(np.int64), expect)
+
+
+def test_inverse_on_random_quantised_coefficients(codec):
+    # any q with |q Q| <= 16384 (the range the quantiser produces) inverts exactly
+    rng = np.random.default_rng(13)
+    for Q in (inputs.step_table(1), inputs.step_table(16), rng.integers(1, 300, 64).astype(np.uint16),
+              np.ones(64, np.uint16)):
+        lim = (16384 // Q.reshape(-1).astype(np.int64)).reshape(8, 8)
+        q = rng.integers(-lim, lim + 1, size=(6, 9, 8, 8)).astype(np.int64)
+        coef = torch.from_numpy(q.astype(np.int16).reshape(1, 6, 9, 8, 8)).to(DEV)
+        dst = torch.empty((48, 72), dtype=torch.uint8, device=DEV)
+        codec.inverse([Image(None, dst, coef)], make_quant(ADCT_Q_STEP, Q))
+        torch.cuda.synchronize()
+        assert np.array_equal(dst.cpu().numpy(), oracle.inverse(q, oracle.MODE_STEP, Q))
+
+
 def test_pitched_and_aliased_images(codec):
     img = inputs.synth_image(3 * 64, 136, 8)  # [1, 192, 136]
     big = torch.zeros((3, 80, 160), dtype=torch.uint8, device=DEV)  # pitch 160, plane stride 80*160
