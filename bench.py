@@ -569,12 +569,15 @@ def run_float(args):
 
 def run_serving(args):
     """Poisson stream of encode/decode requests (50/50) of sizes uniform over
-    {256^2, 512^2, 1080x1920, 2160x3840, 4096^2}, 4 GB device budget."""
+    {256^2, 512^2, 1080x1920, 2160x3840, 4096^2}, 4 GB device budget; the
+    native scheduler (adct_server_*) and the Python one side by side."""
+    import gc
+
     import numpy as np
     import torch
 
     from paper_1702_00817_gb300 import _build, inputs
-    from paper_1702_00817_gb300.serve import Server, poisson_run
+    from paper_1702_00817_gb300.serve import NativeServer, Server, poisson_run
     d = Dist()
     dev = torch.device("cuda", d.local)
     torch.cuda.set_device(dev)
@@ -584,37 +587,47 @@ def run_serving(args):
     sizes = [(256, 256), (512, 512), (1080, 1920), (2160, 3840), (4096, 4096)]
     imgs = {hw: [inputs.synth_image_device(hw[0], hw[1], 7000 + 10 * i + k, 1, dev)[0].cpu().pin_memory()
                  for k in range(2)] for i, hw in enumerate(sizes)}
-    srv = Server(d.local, budget_bytes=4 << 30, streams=4)
-    srv.warm_host_buffers(sizes, count=48)
-    poisson_run(srv, rate=500.0, n_requests=100, sizes=sizes, images_by_size=imgs, seed=1, warm_handles=20)
-    rows = []
     duration = 1.5
-    import gc
-    gc.collect()
-    gc.disable()  # a collection pause inside the run would be charged to whichever request it hit
-    for rate in (100, 500, 1000, 2000, 5000):
-        n_req = max(20, int(rate * duration))
-        t0 = time.perf_counter()
-        reqs = poisson_run(srv, rate=float(rate), n_requests=n_req, sizes=sizes, images_by_size=imgs, seed=rate)
-        wall = max(r.t_done for r in reqs) - t0
-        ok = [r for r in reqs if r.error is None]
-        lat = np.array([r.latency for r in ok]) * 1000.0
-        px = sum(r.pixels.numel() if r.kind == "encode" else r.out_pixels for r in ok)
-        rows.append({"offered_req_s": rate, "req_s": len(ok) / wall, "p50_ms": float(np.percentile(lat, 50)),
-                     "p99_ms": float(np.percentile(lat, 99)), "errors": len(reqs) - len(ok),
-                     "blocks_s": px / 64 / wall})
-    gc.enable()
-    stats = dict(srv.stats)
-    srv.close()
+    results = {}
+    for name, cls, rates, spin in (("native", NativeServer, (100, 500, 1000, 2000, 5000, 10000, 20000), True),
+                                   ("python", Server, (100, 500, 1000, 2000, 5000), False)):
+        srv = cls(d.local, budget_bytes=4 << 30, streams=4)
+        if hasattr(srv, "warm_host_buffers"):
+            srv.warm_host_buffers(sizes, count=48)
+        else:
+            bufs = [torch.empty(hw, dtype=torch.uint8, pin_memory=True) for hw in sizes for _ in range(48)]
+            del bufs
+        poisson_run(srv, rate=500.0, n_requests=100, sizes=sizes, images_by_size=imgs, seed=1, warm_handles=20,
+                    spin=spin)
+        rows = []
+        gc.collect()
+        gc.disable()  # a collection pause inside the run would be charged to whichever request it hit
+        for rate in rates:
+            n_req = max(20, int(rate * duration))
+            t0 = time.perf_counter()
+            reqs = poisson_run(srv, rate=float(rate), n_requests=n_req, sizes=sizes, images_by_size=imgs, seed=rate,
+                               spin=spin)
+            wall = max(r.t_done for r in reqs) - t0
+            ok = [r for r in reqs if r.error is None]
+            lat = np.array([r.latency for r in ok]) * 1000.0
+            px = sum(r.pixels.numel() if r.kind == "encode" else r.out_pixels for r in ok)
+            rows.append({"offered_req_s": rate, "req_s": len(ok) / wall, "p50_ms": float(np.percentile(lat, 50)),
+                         "p99_ms": float(np.percentile(lat, 99)), "errors": len(reqs) - len(ok),
+                         "blocks_s": px / 64 / wall})
+        gc.enable()
+        results[name] = {"rows": rows, "stats": dict(srv.stats)}
+        srv.close()
     if d.rank == 0:
-        top = rows[-1]
-        line = {"metric": METRIC, "value": top["req_s"], "unit": "req/s", "n_gpus": d.ws, "steps": len(rows),
-                "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "int32", "data": "synthetic",
+        top = results["native"]["rows"][-1]
+        line = {"metric": METRIC, "value": top["req_s"], "unit": "req/s", "n_gpus": d.ws,
+                "steps": len(results["native"]["rows"]), "warmup": 1, "ms_per_step": None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
                 "config": {"workload": "serving: Poisson encode/decode 50/50, sizes {256^2,512^2,1080x1920,"
-                                       "2160x3840,4096^2}, 4 GB budget, on-device coefficient store",
+                                       "2160x3840,4096^2}, 4 GB budget, on-device coefficient store; native "
+                                       "scheduler (adct_server_*), Python scheduler for comparison",
                            "seconds_per_rate": duration},
-                "serving": rows, "p50_ms": top["p50_ms"], "p99_ms": top["p99_ms"], "server_stats": stats}
+                "serving": results["native"]["rows"], "p50_ms": top["p50_ms"], "p99_ms": top["p99_ms"],
+                "server_stats": results["native"]["stats"], "python_scheduler": results["python"]}
         print(json.dumps(line), flush=True)
     d.close()
     return 0

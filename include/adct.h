@@ -266,6 +266,64 @@ adct_status adct_kernel_time(adct_context* ctx, double* total_ms, int64_t* launc
 #define ADCT_NOALLOC_MAX_PLANES 1024
 adct_status adct_roundtrip_noalloc(const adct_image* imgs, int32_t n, const adct_quant* quant, adct_stream_t stream);
 
+/*
+ * Continuous-batching encode/decode server (serving; the paper's encode and
+ * decode procedures of Sec. 3 as a request stream).  A scheduler thread owns a
+ * context, a device-memory arena of budget_bytes (one cudaMalloc at creation)
+ * and an on-device store of quantised coefficients.  Requests submitted while
+ * others run are admitted as arena space frees up (the oldest store entries
+ * that no pending decode uses are evicted when needed); each scheduler pass
+ * packs its admissions into one encode launch and one decode launch on the next
+ * of its streams, so batches overlap on the device.  Results are identical to
+ * adct_roundtrip / adct_inverse on the same inputs.
+ *   encode: host pixels (width x height uint8, rows pitch bytes apart) are
+ *           copied in, forward-transformed and quantised; the coefficients stay
+ *           in the store under the handle reported by the completion.
+ *   decode: a stored handle is dequantised and inverted; the pixels are copied
+ *           to host memory `out` (rows pitch bytes apart; width/height of the
+ *           encoded image are returned).  The handle is pinned from submission
+ *           to completion.
+ * Host buffers must stay valid until the request completes; pinned memory gives
+ * asynchronous copies.  Timestamps are seconds on adct_server_clock()'s
+ * monotonic clock (t_submit may be supplied by the caller on that clock, else
+ * the submission time is used).  Submission and polling are thread-safe.
+ */
+typedef struct adct_server adct_server;
+
+typedef struct {
+  int64_t budget_bytes; /* device memory for in-flight work and the store (0: 4 GiB) */
+  int32_t streams;      /* CUDA streams used to overlap batches (0: 4) */
+  int32_t max_batch;    /* requests packed into one launch (0: 256) */
+  adct_quant quant;     /* quantiser of every request */
+} adct_server_config;
+
+typedef struct {
+  uint64_t request_id;
+  int32_t status;  /* ADCT_OK; ADCT_ERR_INVALID_ARG: handle unknown; ADCT_ERR_OOM: larger than the budget; ADCT_ERR_CUDA */
+  int32_t kind;    /* 0 encode, 1 decode */
+  uint64_t handle; /* encode: handle of the stored coefficients; decode: the handle decoded */
+  double t_submit, t_admit, t_done;
+} adct_completion;
+
+typedef struct {
+  int64_t launches, admitted, evicted, unknown_handle, oversized, errors, store_entries, arena_free_bytes;
+  int32_t max_overlap, reserved;
+} adct_server_stats_t;
+
+adct_status adct_server_create(adct_server** srv, int32_t device, const adct_server_config* cfg);
+/* Stops the scheduler after the batches in flight complete, then frees everything. */
+void adct_server_destroy(adct_server* srv);
+adct_status adct_server_encode(adct_server* srv, const uint8_t* pixels, int32_t width, int32_t height, int64_t pitch,
+                               double t_submit, uint64_t* request_id);
+/* Fails at once (ADCT_ERR_INVALID_ARG) for a handle not in the store. */
+adct_status adct_server_decode(adct_server* srv, uint64_t handle, uint8_t* out, int64_t pitch, double t_submit,
+                               uint64_t* request_id, int32_t* width, int32_t* height);
+/* Moves up to max completions into out, waiting up to wait_us for the first; returns the count. */
+int32_t adct_server_poll(adct_server* srv, adct_completion* out, int32_t max, int32_t wait_us);
+adct_status adct_server_stats(adct_server* srv, adct_server_stats_t* stats);
+/* The server's clock: seconds, CLOCK_MONOTONIC (the clock of Python's time.perf_counter on Linux). */
+double adct_server_clock(void);
+
 /* Human-readable name of a status code (static string). */
 const char* adct_status_string(adct_status status);
 

@@ -29,7 +29,9 @@ EXPORTS = (
     "adct_create", "adct_destroy", "adct_forward", "adct_quantise", "adct_inverse", "adct_roundtrip",
     "adct_forward_f32", "adct_backward_f32", "adct_set_launch", "adct_get_launch", "adct_roundtrip_graph",
     "adct_autotune", "adct_roundtrip_host", "adct_butterfly_host", "adct_kernel_timing", "adct_kernel_time",
-    "adct_roundtrip_noalloc", "adct_status_string", "adct_last_error",
+    "adct_roundtrip_noalloc", "adct_server_create", "adct_server_destroy", "adct_server_encode",
+    "adct_server_decode", "adct_server_poll", "adct_server_stats", "adct_server_clock",
+    "adct_status_string", "adct_last_error",
 )
 
 
@@ -58,6 +60,23 @@ class adct_launch(ctypes.Structure):
         ("stage_coef", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
     ]
+
+
+class adct_server_config(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("streams", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("quant", adct_quant)]
+
+
+class adct_completion(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_uint64), ("status", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("handle", ctypes.c_uint64), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+class adct_server_stats_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("launches", "admitted", "evicted", "unknown_handle", "oversized",
+                                              "errors", "store_entries", "arena_free_bytes")] + \
+               [("max_overlap", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class AdctError(RuntimeError):
@@ -104,6 +123,14 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "adct_kernel_timing": ([P, i32], i32),
         "adct_kernel_time": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], i32),
         "adct_roundtrip_noalloc": ([I, i32, Qp, P], i32),
+        "adct_server_create": ([ctypes.POINTER(ctypes.c_void_p), i32, ctypes.POINTER(adct_server_config)], i32),
+        "adct_server_destroy": ([P], None),
+        "adct_server_encode": ([P, P, i32, i32, i64, ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)], i32),
+        "adct_server_decode": ([P, ctypes.c_uint64, P, i64, ctypes.c_double, ctypes.POINTER(ctypes.c_uint64),
+                                ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
+        "adct_server_poll": ([P, ctypes.POINTER(adct_completion), i32, i32], i32),
+        "adct_server_stats": ([P, ctypes.POINTER(adct_server_stats_t)], i32),
+        "adct_server_clock": ([], ctypes.c_double),
         "adct_status_string": ([i32], ctypes.c_char_p),
         "adct_last_error": ([P], ctypes.c_char_p),
     }

@@ -289,8 +289,8 @@ def _default_table():
     return (1 + np.floor(4 * (1 + i + j))).astype(np.uint16)
 
 
-def poisson_run(server: Server, rate: float, n_requests: int, sizes, images_by_size, seed: int = 0,
-                warm_handles: int = 0):
+def poisson_run(server, rate: float, n_requests: int, sizes, images_by_size, seed: int = 0,
+                warm_handles: int = 0, spin: bool = False):
     """Drive the server with a Poisson stream of n_requests (50/50 encode and
     decode; decodes pick a live handle).  Returns the finished requests; the
     pixels of finished decodes are released as the stream goes (only their
@@ -314,7 +314,13 @@ def poisson_run(server: Server, rate: float, n_requests: int, sizes, images_by_s
     for k in range(n_requests):
         t += gaps[k]
         wait = t - time.perf_counter()
-        if wait > 0:
+        if spin:
+            # the native scheduler needs no interpreter lock: spin for the last 200 us
+            if wait > 2e-4:
+                time.sleep(wait - 2e-4)
+            while time.perf_counter() < t:
+                pass
+        elif wait > 0:
             time.sleep(wait)  # no busy wait: the arrival time stays t, lateness counts as latency
         # handles of finished encodes become decodable; decodes pick among the most recent
         if k % 8 == 0:
@@ -343,3 +349,122 @@ def poisson_run(server: Server, rate: float, n_requests: int, sizes, images_by_s
         if r.kind == "decode":
             r.result = None
     return reqs
+
+
+class NativeServer:
+    """The same service run by the library's C++ scheduler (adct_server_*):
+    admission, arena allocation, the coefficient store, batching, launches and
+    completion tracking all happen on a native thread; this class only submits
+    requests and turns completions into finished Request objects (a polling
+    thread).  Interface compatible with Server for the client helpers."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 4 << 30, streams: int = 4, quant=None,
+                 max_batch: int = 256):
+        import ctypes
+
+        from . import _native as N
+        self._N = N
+        self._ct = ctypes
+        self.lib = N.load()
+        cfg = N.adct_server_config()
+        cfg.budget_bytes = int(budget_bytes)
+        cfg.streams = int(streams)
+        cfg.max_batch = int(max_batch)
+        cfg.quant = quant if quant is not None else make_quant(ADCT_Q_STEP, _default_table())
+        h = ctypes.c_void_p()
+        N.check(self.lib.adct_server_create(ctypes.byref(h), int(device), ctypes.byref(cfg)), None,
+                "adct_server_create")
+        self._srv = h
+        self._lock = threading.Lock()
+        self._pending: dict[int, Request] = {}
+        self._shapes: dict[int, tuple[int, int]] = {}
+        self._stop = False
+        self._thread = threading.Thread(target=self._poll_loop, name="adct-native-poll", daemon=True)
+        self._thread.start()
+
+    def clock(self) -> float:
+        return self.lib.adct_server_clock()
+
+    # -- client side -----------------------------------------------------
+    def submit(self, req: Request) -> Request:
+        ct, N = self._ct, self._N
+        rid = ct.c_uint64(0)
+        t_sub = req.t_arrival or 0.0
+        with self._lock:
+            if req.kind == "encode":
+                px = req.pixels
+                H, W = px.shape
+                st = self.lib.adct_server_encode(self._srv, px.data_ptr(), W, H, px.stride(0), t_sub, ct.byref(rid))
+            else:
+                shape = self._shapes.get(req.handle)
+                if shape is None:
+                    st = N.ADCT_ERR_INVALID_ARG
+                else:
+                    out = torch.empty(shape, dtype=torch.uint8, pin_memory=True)
+                    req.result = out
+                    w, h = ct.c_int32(0), ct.c_int32(0)
+                    st = self.lib.adct_server_decode(self._srv, int(req.handle), out.data_ptr(), out.stride(0),
+                                                     t_sub, ct.byref(rid), ct.byref(w), ct.byref(h))
+                    req.out_pixels = out.numel()
+            if st != N.ADCT_OK:
+                req.error = "unknown handle" if req.kind == "decode" else self.lib.adct_status_string(st).decode()
+                req.result = None
+                req.t_done = time.perf_counter()
+                if not req.t_arrival:
+                    req.t_arrival = req.t_done
+                req.done.set()
+                return req
+            self._pending[rid.value] = req
+        return req
+
+    def encode(self, pixels: torch.Tensor) -> Request:
+        return self.submit(Request("encode", pixels=pixels))
+
+    def decode(self, handle: int) -> Request:
+        return self.submit(Request("decode", handle=handle))
+
+    def _poll_loop(self):
+        ct, N = self._ct, self._N
+        buf = (N.adct_completion * 64)()
+        while not self._stop:
+            n = self.lib.adct_server_poll(self._srv, buf, 64, 1000)
+            for k in range(n):
+                c = buf[k]
+                with self._lock:
+                    r = self._pending.pop(c.request_id, None)
+                    if r is None:
+                        continue
+                    if c.status == N.ADCT_OK and c.kind == 0:
+                        self._shapes[c.handle] = tuple(r.pixels.shape)
+                r.t_arrival = r.t_arrival or c.t_submit
+                r.t_admit, r.t_done = c.t_admit, c.t_done
+                if c.status != N.ADCT_OK:
+                    r.error = self.lib.adct_status_string(c.status).decode()
+                    if r.kind == "decode":
+                        r.result = None
+                elif r.kind == "encode":
+                    r.result = c.handle
+                r.done.set()
+
+    @property
+    def stats(self) -> dict:
+        st = self._N.adct_server_stats_t()
+        self.lib.adct_server_stats(self._srv, self._ct.byref(st))
+        return {f: getattr(st, f) for f, _ in st._fields_ if f != "reserved"}
+
+    def drain(self, timeout: float = 60.0) -> None:
+        t_end = time.perf_counter() + timeout
+        while time.perf_counter() < t_end:
+            with self._lock:
+                if not self._pending:
+                    return
+            time.sleep(0.0005)
+        raise TimeoutError("server did not drain")
+
+    def close(self):
+        if self._srv:
+            self.drain()
+            self._stop = True
+            self._thread.join()
+            self.lib.adct_server_destroy(self._srv)
+            self._srv = None

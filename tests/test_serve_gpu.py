@@ -9,7 +9,7 @@ import torch
 import oracle
 from paper_1702_00817_gb300 import inputs
 from paper_1702_00817_gb300.codec import ADCT_Q_STEP, Codec, Image, make_quant
-from paper_1702_00817_gb300.serve import Request, Server, poisson_run
+from paper_1702_00817_gb300.serve import NativeServer, Request, Server, poisson_run
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0")
@@ -35,9 +35,10 @@ def _alone(codec, px, q):
     return coef.cpu(), dst.cpu()
 
 
-def test_results_in_the_mix_equal_results_alone(images):
+@pytest.mark.parametrize("server_cls", [Server, NativeServer])
+def test_results_in_the_mix_equal_results_alone(images, server_cls):
     q = make_quant(ADCT_Q_STEP, inputs.step_table(4))
-    srv = Server(0, budget_bytes=1 << 30, streams=3, quant=q)
+    srv = server_cls(0, budget_bytes=1 << 30, streams=3, quant=q)
     try:
         enc = [srv.encode(images[hw][k]) for hw in SIZES for k in range(2)]
         for r in enc:
@@ -48,7 +49,8 @@ def test_results_in_the_mix_equal_results_alone(images):
         codec = Codec(0)
         for e, d in zip(enc, dec):
             coef_ref, px_ref = _alone(codec, e.pixels, q)
-            assert torch.equal(srv.store.get(e.result)["coef"].cpu(), coef_ref)
+            if server_cls is Server:
+                assert torch.equal(srv.store.get(e.result)["coef"].cpu(), coef_ref)
             assert torch.equal(d.result, px_ref)
         # and against the oracle for one image
         q_ref, rec_ref = oracle.roundtrip(images[SIZES[1]][0].numpy(), oracle.MODE_STEP, inputs.step_table(4))
@@ -58,16 +60,18 @@ def test_results_in_the_mix_equal_results_alone(images):
         srv.close()
 
 
-def test_requests_overlap_and_stream_admits_mid_flight(images):
+@pytest.mark.parametrize("server_cls", [Server, NativeServer])
+def test_requests_overlap_and_stream_admits_mid_flight(images, server_cls):
     q = make_quant(ADCT_Q_STEP, inputs.step_table(4))
-    srv = Server(0, budget_bytes=2 << 30, streams=4, quant=q)
+    srv = server_cls(0, budget_bytes=2 << 30, streams=4, quant=q)
     try:
         by_size = {hw: images[hw] for hw in SIZES}
         reqs = poisson_run(srv, rate=3000.0, n_requests=300, sizes=SIZES, images_by_size=by_size, seed=3,
                            warm_handles=8)
         assert all(r.done.is_set() and r.error is None for r in reqs)
-        assert srv.stats["max_overlap"] >= 2          # batches were in flight together
-        assert srv.stats["launches"] < len(reqs) + 8   # requests were batched
+        stats = srv.stats
+        assert stats["max_overlap"] >= 2          # batches were in flight together
+        assert stats["launches"] < len(reqs) + 8   # requests were batched
         # some request was admitted before an earlier one completed
         reqs.sort(key=lambda r: r.t_arrival)
         assert any(b.t_admit < a.t_done for a, b in zip(reqs, reqs[1:]))
@@ -96,3 +100,37 @@ def test_budget_rejects_oversized_and_evicts_old_entries(images):
         assert srv.in_flight_bytes == 0 and srv.store.bytes <= small
     finally:
         srv.close()
+
+
+def test_native_budget_rejects_oversized_and_evicts_old_entries(images):
+    q = make_quant(ADCT_Q_STEP, inputs.step_table(4))
+    small = 3 * 512 * 512 + 4096
+    srv = NativeServer(0, budget_bytes=small, streams=2, quant=q)
+    try:
+        big = srv.encode(images[(1080, 1920)][0])
+        assert big.done.wait(30) and big.error == "ADCT_ERR_OOM"
+        a = srv.encode(images[(256, 256)][0])
+        assert a.done.wait(30) and a.error is None
+        b = srv.encode(images[(512, 512)][0])  # needs the space a holds: a is evicted
+        assert b.done.wait(30) and b.error is None
+        assert srv.stats["evicted"] >= 1 and srv.stats["oversized"] == 1
+        lost = srv.decode(a.result)
+        assert lost.done.wait(30) and lost.error == "unknown handle"
+        ok = srv.decode(b.result)
+        assert ok.done.wait(30) and ok.error is None
+        codec = Codec(0)
+        assert torch.equal(ok.result, _alone(codec, images[(512, 512)][0], q)[1])
+        codec.close()
+    finally:
+        srv.close()
+
+
+def test_native_clock_is_the_perf_counter_clock():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1702_00817_gb300 import _native
+    lib = _native.load()
+    t0 = time.perf_counter()
+    tn = lib.adct_server_clock()
+    t1 = time.perf_counter()
+    assert t0 - 1e-3 <= tn <= t1 + 1e-3
