@@ -41,7 +41,7 @@ def parse():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["roundtrip", "ragged", "float", "serving"], default="roundtrip")
+    p.add_argument("--workload", choices=["roundtrip", "ragged", "float", "serving", "quality"], default="roundtrip")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--images", type=int, default=N_IMG)
@@ -633,12 +633,74 @@ def run_serving(args):
     return 0
 
 
+def run_quality(args):
+    """The image experiment's protocol (Sec. 3, Fig. 2) on synthetic stand-ins:
+    45 greyscale 512x512 images, zonal retention of r = 2..45 zig-zag
+    coefficients with the 14-addition transform and with the exact DCT; mean
+    PSNR over images and the percentage error of the mean MSE relative to the
+    DCT, plus the throughput of the quality kernels."""
+    import math
+
+    import torch
+
+    from paper_1702_00817_gb300 import _build, inputs
+    from paper_1702_00817_gb300.codec import ADCT_Q_ZONAL, Codec, Image, make_quant
+    d = Dist()
+    dev = torch.device("cuda", d.local)
+    torch.cuda.set_device(dev)
+    if d.rank == 0 or not _build.up_to_date():
+        _build.build()
+    d.barrier()
+    n, side = 45, 512
+    host = inputs.synth_batch(n, side, side, base_seed=inputs.BASE_SEED + d.rank * n)[:, 0]
+    src = torch.from_numpy(host).to(dev)
+    images = [Image(src[k]) for k in range(n)]
+    codec = Codec(d.local)
+    blocks = n * (side // 8) ** 2
+    rows = []
+    stream = torch.cuda.current_stream(dev)
+    t_adct = t_dct = 0.0
+    for r in range(2, 46):
+        q = make_quant(ADCT_Q_ZONAL, None, r)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sa = codec.quality(images, q)
+        e1.record(stream)
+        sd = codec.quality_dct(images, r)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        t_adct += e0.elapsed_time(e1)
+        t_dct += e1.elapsed_time(e2)
+        mse_a = sa.double().cpu() / (side * side)
+        mse_d = sd.double().cpu() / (side * side)
+        psnr = lambda m: sum(10 * math.log10(255.0 ** 2 / max(float(v), 1e-12)) for v in m) / len(m)
+        ma, md = float(mse_a.mean()), float(mse_d.mean())
+        rows.append({"r": r, "compression_pct": 100.0 * (1 - r / 64), "psnr_adct": psnr(mse_a),
+                     "psnr_dct": psnr(mse_d), "mse_adct": ma, "mse_dct": md,
+                     "ape_mse_pct": 100.0 * abs(ma - md) / md})
+    value = blocks * 44 / (t_adct / 1000.0)
+    if d.rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": d.ws, "steps": 44, "warmup": 0,
+                "ms_per_step": t_adct / 44, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int32", "data": "synthetic (stand-in for the paper's 45-image bank)",
+                "config": {"workload": "quality sweep: 45 x 512x512 u8, zonal r = 2..45, 14-addition transform vs "
+                                       "exact DCT (float32), per-image squared error", "images": n},
+                "dct_blocks_s": blocks * 44 / (t_dct / 1000.0), "sweep": rows,
+                "r25": next(x for x in rows if x["r"] == 25)}
+        print(json.dumps(line), flush=True)
+    codec.close()
+    d.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     return {"roundtrip": run_roundtrip, "ragged": run_ragged, "float": run_float,
-            "serving": run_serving}[args.workload](args)
+            "serving": run_serving, "quality": run_quality}[args.workload](args)
 
 
 if __name__ == "__main__":

@@ -164,6 +164,28 @@ adct_status adct_roundtrip(adct_context* ctx, const adct_image* imgs, int32_t n,
                            adct_stream_t stream);
 
 /*
+ * Quality of the round trip (Sec. 3, the figures of merit of the image
+ * experiment): runs forward, quantise, dequantise and inverse like
+ * adct_roundtrip but writes no pixels or coefficients; instead sse[p] receives
+ * the sum over plane p of (reconstructed pixel - src pixel)^2 (exact, 64-bit).
+ * Planes are numbered image by image, channel by channel.  Uses src only.
+ * sse: DEVICE array of one uint64 per plane (8-byte aligned), overwritten.
+ * MSE = sse / (width * height); PSNR = 10 log10(255^2 / MSE).
+ */
+adct_status adct_quality(adct_context* ctx, const adct_image* imgs, int32_t n, const adct_quant* quant, uint64_t* sse,
+                         adct_stream_t stream);
+
+/*
+ * The exact-DCT comparator of the quality experiment (Sec. 3 compares the
+ * approximation against the DCT): zonal round trip with the orthonormal 8x8
+ * DCT-II in float32, keeping the first r zig-zag coefficients, reconstruction
+ * rounded to nearest (ties to even) and clamped to 0..255; sse as for
+ * adct_quality.  r in 0..64.
+ */
+adct_status adct_quality_dct(adct_context* ctx, const adct_image* imgs, int32_t n, int32_t r, uint64_t* sse,
+                             adct_stream_t stream);
+
+/*
  * Differentiable float32 variant (Sec. 2 C^ = D T).  x, y: [planes][H][W]
  * float32 row-major device tensors (H, W multiples of 8, 16-byte aligned).
  * y = D T x T^T D per 8x8 block, followed, when Qsoft (HOST array of 64

@@ -55,8 +55,10 @@ def _load():
             lib.oracle_roundtrip.argtypes = [P, i64, P, i64, i32, i32, i32, P, i32, P, P]
             lib.oracle_forward_f64.argtypes = [P, i64, i32, i32, P, P, P]
             lib.oracle_backward_f64.argtypes = [P, P, i64, i32, i32, P, P]
+            lib.oracle_dct_matrix.argtypes = [P]
+            lib.oracle_dct_zonal.argtypes = [P, i64, i32, i32, i32, P, i64]
             for f in ("oracle_forward", "oracle_quantise", "oracle_inverse", "oracle_roundtrip",
-                      "oracle_forward_f64", "oracle_backward_f64"):
+                      "oracle_forward_f64", "oracle_backward_f64", "oracle_dct_zonal"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -180,3 +182,25 @@ def backward_f64(x: np.ndarray, gz: np.ndarray, Qsoft=None) -> np.ndarray:
     if _load().oracle_backward_f64(_p(xc), _p(gc), planes, H, W, _p(Qs), _p(gx)) != 0:
         raise ValueError("oracle_backward_f64: bad shape")
     return gx
+
+
+def dct_matrix() -> np.ndarray:
+    out = np.zeros(64, np.float64)
+    _load().oracle_dct_matrix(_p(out))
+    return out.reshape(8, 8)
+
+
+def dct_zonal(plane: np.ndarray, r: int) -> np.ndarray:
+    """Exact-DCT zonal round trip of a uint8 plane keeping r zig-zag coefficients (Sec. 3 comparator)."""
+    x = np.ascontiguousarray(_plane(plane))
+    H, W = x.shape
+    dst = np.zeros_like(x)
+    if _load().oracle_dct_zonal(_p(x), W, W, H, int(r), _p(dst), W) != 0:
+        raise ValueError("oracle_dct_zonal: bad parameters")
+    return dst
+
+
+def sse(a: np.ndarray, b: np.ndarray) -> int:
+    """Sum of squared differences of two uint8 planes (exact)."""
+    d = a.astype(np.int64) - b.astype(np.int64)
+    return int((d * d).sum())

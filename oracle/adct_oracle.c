@@ -315,3 +315,59 @@ int oracle_backward_f64(const double* x, const double* gz, int64_t planes, int32
       }
   return 0;
 }
+
+/* ---------------- exact-DCT comparator (double precision) ---------------- */
+
+/* Sec. 3 compares the approximation against the exact DCT: the orthonormal 8x8
+ * DCT-II, C[k][j] = alpha_k cos(pi (2j + 1) k / 16), alpha_0 = 1/sqrt(8),
+ * alpha_k = 1/2.  Keep the first r zig-zag coefficients of C (X - 128) C^T,
+ * invert with C^T Y C, add 128, round to nearest (ties to even) and clamp to
+ * 0..255.  Returns 0, or -1 on a bad shape or r. */
+void oracle_dct_matrix(double out[64]) {
+  for (int k = 0; k < 8; ++k)
+    for (int j = 0; j < 8; ++j)
+      out[k * 8 + j] = (k == 0 ? sqrt(0.125) : 0.5) * cos(M_PI * (2 * j + 1) * k / 16.0);
+}
+
+int oracle_dct_zonal(const uint8_t* src, int64_t pitch, int32_t width, int32_t height, int32_t r, uint8_t* dst,
+                     int64_t dst_pitch) {
+  if (check_plane(width, height, pitch) || check_plane(width, height, dst_pitch) || r < 0 || r > 64) return -1;
+  double C[64];
+  int32_t rank[64];
+  oracle_dct_matrix(C);
+  oracle_zigzag_rank(rank);
+  for (int by = 0; by < height / 8; ++by)
+    for (int bx = 0; bx < width / 8; ++bx) {
+      double x[64], Y[64], T1[64];
+      for (int i = 0; i < 8; ++i)
+        for (int j = 0; j < 8; ++j) x[i * 8 + j] = (double)src[(int64_t)(8 * by + i) * pitch + 8 * bx + j] - 128.0;
+      for (int k = 0; k < 8; ++k) /* T1 = C x */
+        for (int j = 0; j < 8; ++j) {
+          double acc = 0;
+          for (int i = 0; i < 8; ++i) acc += C[k * 8 + i] * x[i * 8 + j];
+          T1[k * 8 + j] = acc;
+        }
+      for (int k = 0; k < 8; ++k) /* Y = T1 C^T, zonal mask */
+        for (int l = 0; l < 8; ++l) {
+          double acc = 0;
+          for (int j = 0; j < 8; ++j) acc += T1[k * 8 + j] * C[l * 8 + j];
+          Y[k * 8 + l] = rank[k * 8 + l] < r ? acc : 0.0;
+        }
+      for (int i = 0; i < 8; ++i) /* T1 = C^T Y */
+        for (int l = 0; l < 8; ++l) {
+          double acc = 0;
+          for (int k = 0; k < 8; ++k) acc += C[k * 8 + i] * Y[k * 8 + l];
+          T1[i * 8 + l] = acc;
+        }
+      for (int i = 0; i < 8; ++i) /* X^ = T1 C, rounded and clamped */
+        for (int j = 0; j < 8; ++j) {
+          double acc = 0;
+          for (int l = 0; l < 8; ++l) acc += T1[i * 8 + l] * C[l * 8 + j];
+          double p = rint(acc + 128.0);
+          if (p < 0) p = 0;
+          if (p > 255) p = 255;
+          dst[(int64_t)(8 * by + i) * dst_pitch + 8 * bx + j] = (uint8_t)p;
+        }
+    }
+  return 0;
+}

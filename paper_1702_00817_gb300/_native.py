@@ -29,7 +29,7 @@ EXPORTS = (
     "adct_create", "adct_destroy", "adct_forward", "adct_quantise", "adct_inverse", "adct_roundtrip",
     "adct_forward_f32", "adct_backward_f32", "adct_set_launch", "adct_get_launch", "adct_roundtrip_graph",
     "adct_autotune", "adct_roundtrip_host", "adct_butterfly_host", "adct_kernel_timing", "adct_kernel_time",
-    "adct_roundtrip_noalloc", "adct_server_create", "adct_server_destroy", "adct_server_encode",
+    "adct_roundtrip_noalloc", "adct_quality", "adct_quality_dct", "adct_server_create", "adct_server_destroy", "adct_server_encode",
     "adct_server_decode", "adct_server_poll", "adct_server_stats", "adct_server_clock",
     "adct_status_string", "adct_last_error",
 )
@@ -123,6 +123,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "adct_kernel_timing": ([P, i32], i32),
         "adct_kernel_time": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], i32),
         "adct_roundtrip_noalloc": ([I, i32, Qp, P], i32),
+        "adct_quality": ([P, I, i32, Qp, P, P], i32),
+        "adct_quality_dct": ([P, I, i32, i32, P, P], i32),
         "adct_server_create": ([ctypes.POINTER(ctypes.c_void_p), i32, ctypes.POINTER(adct_server_config)], i32),
         "adct_server_destroy": ([P], None),
         "adct_server_encode": ([P, P, i32, i32, i64, ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)], i32),

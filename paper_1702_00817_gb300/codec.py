@@ -199,6 +199,26 @@ class Codec:
         st = self.lib.adct_roundtrip_host(self.ctx, arr, len(images), ctypes.byref(quant), int(chunk_bytes))
         N.check(st, self.ctx, "adct_roundtrip_host")
 
+    def quality(self, images, quant, stream=None) -> torch.Tensor:
+        """Per-plane sum of squared round-trip error (int64 tensor on the device)."""
+        arr = image_array(images)
+        planes = sum(image_struct(im).channels for im in images)
+        sse = torch.empty(max(1, planes), dtype=torch.int64, device=torch.device("cuda", self.device))
+        st = self.lib.adct_quality(self.ctx, arr, len(images), ctypes.byref(quant), sse.data_ptr(),
+                                   _stream_handle(self.device, stream))
+        N.check(st, self.ctx, "adct_quality")
+        return sse[:planes]
+
+    def quality_dct(self, images, r: int, stream=None) -> torch.Tensor:
+        """Per-plane sum of squared error of the exact-DCT zonal round trip keeping r coefficients."""
+        arr = image_array(images)
+        planes = sum(image_struct(im).channels for im in images)
+        sse = torch.empty(max(1, planes), dtype=torch.int64, device=torch.device("cuda", self.device))
+        st = self.lib.adct_quality_dct(self.ctx, arr, len(images), int(r), sse.data_ptr(),
+                                       _stream_handle(self.device, stream))
+        N.check(st, self.ctx, "adct_quality_dct")
+        return sse[:planes]
+
     def kernel_timing(self, enable: bool):
         N.check(self.lib.adct_kernel_timing(self.ctx, 1 if enable else 0), self.ctx, "adct_kernel_timing")
 

@@ -311,13 +311,14 @@ int need_for_kind(int kind) {
     case K_INVERSE: return NEED_COEF | NEED_DST;
     case K_RT_FULL: return NEED_SRC | NEED_COEF | NEED_DST;
     case K_RT_PIX: return NEED_SRC | NEED_DST;
+    case K_RT_SSE: return NEED_SRC;
     default: return NEED_SRC | NEED_COEF;
   }
 }
 
 // Validates, uploads the descriptor table through a workspace slot and launches.
 adct_status run_codec(adct_context* ctx, const adct_image* imgs, int32_t n, const adct_quant* quant, int kind,
-                      cudaStream_t stream, const LaunchShape& shape) {
+                      cudaStream_t stream, const LaunchShape& shape, unsigned long long* sse = nullptr) {
   if (!ctx) return ADCT_ERR_INVALID_ARG;
   ctx->last_error.clear();
   adct_status st = check_shape(ctx, shape);
@@ -351,6 +352,10 @@ adct_status run_codec(adct_context* ctx, const adct_image* imgs, int32_t n, cons
   cl.planes = (const PlaneDesc*)slot->dev;
   cl.starts = (const int64_t*)((char*)slot->dev + planes.size() * sizeof(PlaneDesc));
   cl.nplanes = (int32_t)planes.size();
+  if (kind == K_RT_SSE) {
+    cl.sse = sse;
+    ADCT_CUDA(ctx, cudaMemsetAsync(sse, 0, planes.size() * sizeof(unsigned long long), stream));
+  }
   TimedLaunch tl(ctx, stream);
   cudaError_t e = launch_codec(cl, shape, ctx->sm_count, stream);
   tl.done();
@@ -555,6 +560,62 @@ adct_status adct_roundtrip(adct_context* ctx, const adct_image* imgs, int32_t n,
   if (!ok) return fail(ctx, ADCT_ERR_INVALID_ARG, "coef/dst must be set on all images or on none");
   if (n > 0 && !imgs[0].coef && !imgs[0].dst) return fail(ctx, ADCT_ERR_INVALID_ARG, "need coef or dst");
   return run_codec(ctx, imgs, n, quant, kind, (cudaStream_t)stream, ctx->shape);
+}
+
+adct_status adct_quality(adct_context* ctx, const adct_image* imgs, int32_t n, const adct_quant* quant, uint64_t* sse,
+                         adct_stream_t stream) {
+  if (!ctx) return ADCT_ERR_INVALID_ARG;
+  if (n > 0 && !sse) return fail(ctx, ADCT_ERR_INVALID_ARG, "sse is NULL");
+  if ((uintptr_t)sse % 8) return fail(ctx, ADCT_ERR_ALIGN, "sse must be 8-byte aligned");
+  return run_codec(ctx, imgs, n, quant, K_RT_SSE, (cudaStream_t)stream, ctx->shape, (unsigned long long*)sse);
+}
+
+adct_status adct_quality_dct(adct_context* ctx, const adct_image* imgs, int32_t n, int32_t r, uint64_t* sse,
+                             adct_stream_t stream) {
+  if (!ctx) return ADCT_ERR_INVALID_ARG;
+  ctx->last_error.clear();
+  if (r < 0 || r > 64) return fail(ctx, ADCT_ERR_INVALID_ARG, "r outside 0..64");
+  if (n > 0 && !sse) return fail(ctx, ADCT_ERR_INVALID_ARG, "sse is NULL");
+  if ((uintptr_t)sse % 8) return fail(ctx, ADCT_ERR_ALIGN, "sse must be 8-byte aligned");
+  std::vector<PlaneDesc> planes;
+  std::vector<int64_t> starts;
+  adct_status st = build_planes(ctx, imgs, n, NEED_SRC, planes, starts);
+  if (st != ADCT_OK) return st;
+  if (starts.back() == 0) return ADCT_OK;
+  // the orthonormal DCT-II matrix and the zig-zag zonal mask
+  float c[64];
+  for (int k = 0; k < 8; ++k)
+    for (int j = 0; j < 8; ++j)
+      c[8 * k + j] = (float)((k == 0 ? std::sqrt(0.125) : 0.5) * std::cos(M_PI * (2 * j + 1) * k / 16.0));
+  int rank[64];
+  zigzag_rank(rank);
+  uint64_t mask = 0;
+  for (int k = 0; k < 64; ++k)
+    if (rank[k] < r) mask |= 1ull << k;
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = table_bytes(planes.size());
+  Slot* slot = find_cached_slot(ctx, planes, starts, s);
+  if (!slot) {
+    st = acquire_slot(ctx, bytes, &slot);
+    if (st != ADCT_OK) return st;
+    fill_table(slot->host, planes, starts);
+    ADCT_CUDA(ctx, cudaMemcpyAsync(slot->dev, slot->host, bytes, cudaMemcpyHostToDevice, s));
+    ADCT_CUDA(ctx, cudaEventRecord(slot->uploaded, s));
+    slot->bytes = bytes;
+  }
+  ADCT_CUDA(ctx, cudaMemsetAsync(sse, 0, planes.size() * sizeof(uint64_t), s));
+  TimedLaunch tl(ctx, s);
+  cudaError_t e = launch_dct_quality((const PlaneDesc*)slot->dev,
+                                     (const int64_t*)((char*)slot->dev + planes.size() * sizeof(PlaneDesc)),
+                                     (int32_t)planes.size(), starts.back(), c, mask, (unsigned long long*)sse,
+                                     ctx->sm_count, s);
+  tl.done();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "dct quality launch");
+  ADCT_CUDA(ctx, cudaEventRecord(slot->done, s));
+  slot->pending = true;
+  slot->stream = s;
+  return ADCT_OK;
 }
 
 adct_status adct_forward_f32(adct_context* ctx, const float* x, float* y, int64_t planes, int32_t H, int32_t W,

@@ -82,10 +82,13 @@ constexpr int32_t kDcBias = 32 + 128 * 64;
 
 template <int KIND>
 struct KindTraits {
-  static constexpr bool in_pix = (KIND == K_FORWARD || KIND == K_RT_FULL || KIND == K_RT_PIX || KIND == K_RT_COEF);
-  static constexpr bool quant = (KIND == K_QUANTISE || KIND == K_RT_FULL || KIND == K_RT_PIX || KIND == K_RT_COEF);
+  static constexpr bool in_pix =
+      (KIND == K_FORWARD || KIND == K_RT_FULL || KIND == K_RT_PIX || KIND == K_RT_COEF || KIND == K_RT_SSE);
+  static constexpr bool quant =
+      (KIND == K_QUANTISE || KIND == K_RT_FULL || KIND == K_RT_PIX || KIND == K_RT_COEF || KIND == K_RT_SSE);
   static constexpr bool write_coef = (KIND == K_FORWARD || KIND == K_QUANTISE || KIND == K_RT_FULL || KIND == K_RT_COEF);
-  static constexpr bool inv = (KIND == K_INVERSE || KIND == K_RT_FULL || KIND == K_RT_PIX);
+  static constexpr bool inv = (KIND == K_INVERSE || KIND == K_RT_FULL || KIND == K_RT_PIX || KIND == K_RT_SSE);
+  static constexpr bool sse = (KIND == K_RT_SSE);  // compare with the input instead of storing pixels
 };
 
 // Position of one lane's block: plane index and block coordinates (by, bx);
@@ -171,11 +174,11 @@ struct SmemPlan {
 // Arithmetic of one 8x8 block: read its input from the input stage, quantise,
 // stage or store q, dequantise, invert and store the pixels.
 template <int KIND, int QMODE, bool EVENQ>
-__device__ __forceinline__ void block_step(const uint8_t* __restrict__ in, uint8_t* __restrict__ stage_out,
-                                           const PlaneDesc* __restrict__ planes, const Pos& pos, int stage_coef,
-                                           const QuantParams& qp, int lane) {
+__device__ __forceinline__ uint32_t block_step(const uint8_t* __restrict__ in, uint8_t* __restrict__ stage_out,
+                                               const PlaneDesc* __restrict__ planes, const Pos& pos, int stage_coef,
+                                               const QuantParams& qp, int lane) {
   using KT = KindTraits<KIND>;
-  if (pos.plane < 0) return;
+  if (pos.plane < 0) return 0;
   const PlaneDesc* d = planes + pos.plane;
   int32_t v[64];
   if (KT::in_pix) {
@@ -247,18 +250,33 @@ __device__ __forceinline__ void block_step(const uint8_t* __restrict__ in, uint8
   }
 
   // ---- inverse (8 column, then 8 row transposed butterflies) and output ----
+  uint32_t err = 0;
   if (KT::inv) {
     inv2d(v);
-    const int64_t pitch = __ldg(&d->pitch);
-    uint8_t* o = dst_of(d) + (int64_t)(8 * pos.by) * pitch + 8 * pos.bx;
+    if (KT::sse) {
+      // squared error against the input rows, still in the input stage
+      const uint2* st = (const uint2*)in;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      uint2 w;
-      w.x = pixels4(v[8 * i + 0], v[8 * i + 1], v[8 * i + 2], v[8 * i + 3]);
-      w.y = pixels4(v[8 * i + 4], v[8 * i + 5], v[8 * i + 6], v[8 * i + 7]);
-      __stcs((uint2*)(o + i * pitch), w);
+      for (int i = 0; i < 8; ++i) {
+        const uint2 x = st[i * 32 + lane];
+        const uint32_t e0 = __vabsdiffu4(pixels4(v[8 * i + 0], v[8 * i + 1], v[8 * i + 2], v[8 * i + 3]), x.x);
+        const uint32_t e1 = __vabsdiffu4(pixels4(v[8 * i + 4], v[8 * i + 5], v[8 * i + 6], v[8 * i + 7]), x.y);
+        err = __dp4a(e0, e0, err);
+        err = __dp4a(e1, e1, err);
+      }
+    } else {
+      const int64_t pitch = __ldg(&d->pitch);
+      uint8_t* o = dst_of(d) + (int64_t)(8 * pos.by) * pitch + 8 * pos.bx;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        uint2 w;
+        w.x = pixels4(v[8 * i + 0], v[8 * i + 1], v[8 * i + 2], v[8 * i + 3]);
+        w.y = pixels4(v[8 * i + 4], v[8 * i + 5], v[8 * i + 6], v[8 * i + 7]);
+        __stcs((uint2*)(o + i * pitch), w);
+      }
     }
   }
+  return err;
 }
 
 // Write a staged 32-block half-tile of coefficients back with 512-byte warp
@@ -296,7 +314,7 @@ __device__ __forceinline__ void write_back(const uint8_t* __restrict__ stage_out
 template <int KIND, int QMODE, bool EVENQ>
 __global__ void __launch_bounds__(kMaxThreads, 3)
 k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts, int32_t nplanes, int64_t total,
-        int64_t chunk, int stage_coef, const QuantParams qp) {
+        int64_t chunk, int stage_coef, unsigned long long* __restrict__ sse, const QuantParams qp) {
   using KT = KindTraits<KIND>;
   using SP = SmemPlan<KIND>;
   constexpr int kTile = 32 * kBpl;
@@ -353,6 +371,8 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
     cp_async_commit();
   };
 
+  unsigned long long acc = 0;  // K_RT_SSE: this lane's error sum for plane acc_plane
+  int acc_plane = -1;
   Pos pc[kBpl];
 #pragma unroll
   for (int u = 0; u < kBpl; ++u) pc[u] = cur.locate(planes, starts, begin, 32 * u + lane, rend);
@@ -370,9 +390,19 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
     __syncwarp();
 
 #pragma unroll
-    for (int u = 0; u < kBpl; ++u)
-      block_step<KIND, QMODE, EVENQ>(wsm + s * SP::in_stage + u * SP::in_per32, stage_out + u * kTileBytesOut,
-                                     planes, pc[u], stage_coef, qp, lane);
+    for (int u = 0; u < kBpl; ++u) {
+      const uint32_t e = block_step<KIND, QMODE, EVENQ>(wsm + s * SP::in_stage + u * SP::in_per32,
+                                                        stage_out + u * kTileBytesOut, planes, pc[u], stage_coef, qp,
+                                                        lane);
+      if (KT::sse && pc[u].plane >= 0) {
+        if (pc[u].plane != acc_plane) {  // one atomic per lane per plane it visits
+          if (acc_plane >= 0) atomicAdd(sse + acc_plane, acc);
+          acc_plane = pc[u].plane;
+          acc = 0;
+        }
+        acc += e;
+      }
+    }
 
     if (KT::write_coef && stage_coef) {
       __syncwarp();
@@ -383,10 +413,12 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
 #pragma unroll
     for (int u = 0; u < kBpl; ++u) pc[u] = pn[u];
   }
+  if (KT::sse && acc_plane >= 0) atomicAdd(sse + acc_plane, acc);
   cp_async_wait<0>();
 }
 
-using KernelFn = void (*)(const PlaneDesc*, const int64_t*, int32_t, int64_t, int64_t, int, const QuantParams);
+using KernelFn = void (*)(const PlaneDesc*, const int64_t*, int32_t, int64_t, int64_t, int, unsigned long long*,
+                          const QuantParams);
 
 template <int KIND, bool EVENQ>
 KernelFn pick_mode(int qmode) {
@@ -413,6 +445,7 @@ KernelFn pick_kernel_q(int kind, int qmode) {
     case K_RT_FULL: return pick_mode<K_RT_FULL, EVENQ>(qmode);
     case K_RT_PIX: return pick_mode<K_RT_PIX, EVENQ>(qmode);
     case K_RT_COEF: return pick_mode<K_RT_COEF, EVENQ>(qmode);
+    case K_RT_SSE: return pick_mode<K_RT_SSE, EVENQ>(qmode);
     default: return nullptr;
   }
 }
@@ -431,6 +464,7 @@ int warp_smem(int kind) {
     case K_INVERSE: return SmemPlan<K_INVERSE>::warp;
     case K_RT_FULL: return SmemPlan<K_RT_FULL>::warp;
     case K_RT_PIX: return SmemPlan<K_RT_PIX>::warp;
+    case K_RT_SSE: return SmemPlan<K_RT_SSE>::warp;
     default: return SmemPlan<K_RT_COEF>::warp;
   }
 }
@@ -467,7 +501,8 @@ cudaError_t launch_codec(const CodecLaunch& c, const LaunchShape& shape, int sm_
   const int64_t warps = (int64_t)grid * (shape.threads / 32);
   int64_t chunk = (c.total + warps - 1) / warps;
   chunk = (chunk + 32 * kBpl - 1) / (32 * kBpl) * (32 * kBpl);
-  fn<<<grid, shape.threads, smem, stream>>>(c.planes, c.starts, c.nplanes, c.total, chunk, shape.stage_coef, c.qp);
+  fn<<<grid, shape.threads, smem, stream>>>(c.planes, c.starts, c.nplanes, c.total, chunk, shape.stage_coef, c.sse,
+                                            c.qp);
   return cudaGetLastError();
 }
 

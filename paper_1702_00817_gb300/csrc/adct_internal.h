@@ -17,6 +17,7 @@ enum Kind {
   K_RT_FULL = 3,  // src -> coef (q) and dst
   K_RT_PIX = 4,   // src -> dst (q not stored)
   K_RT_COEF = 5,  // src -> coef (q), no reconstruction (encode)
+  K_RT_SSE = 6,   // src -> round trip -> squared error against src per plane (nothing stored)
 };
 
 struct LaunchShape {
@@ -33,6 +34,7 @@ struct CodecLaunch {
   int kind;                 // Kind
   int qmode;                // QMode (quantiser applied by QUANTISE / RT kinds)
   bool evenq;               // the step table has an even step <= 16384 (tie correction needed)
+  unsigned long long* sse;  // K_RT_SSE: per-plane sums of squared reconstruction error (device)
   QuantParams qp;
 };
 
@@ -42,6 +44,12 @@ cudaError_t launch_codec(const CodecLaunch& c, const LaunchShape& shape, int sm_
 // Largest grid the persistent kernel uses for this shape (CTAs), and its dynamic shared memory.
 int codec_grid(const LaunchShape& shape, int sm_count, int64_t total);
 size_t codec_smem_bytes(const LaunchShape& shape, int kind);
+
+// Exact-DCT comparator of the quality sweep: zonal round trip of every block
+// with the orthonormal 8x8 DCT-II in float32; per-plane squared error.
+cudaError_t launch_dct_quality(const PlaneDesc* planes, const int64_t* starts, int32_t nplanes, int64_t total,
+                               const float* dct64, uint64_t keep_mask, unsigned long long* sse, int sm_count,
+                               cudaStream_t stream);
 
 // Float variant (Sec. 2 C^ = D T): forward (optionally soft-quantised) and adjoint.
 struct FloatParams {

@@ -275,3 +275,32 @@ def test_float_adjoint_matches_central_finite_differences(Qkind):
         fd = (f(x + h * v) - f(x - h * v)) / (2 * h)
         an = float((gx * v).sum())
         assert abs(fd - an) <= 1e-4 * max(1.0, abs(an))
+
+
+def test_dct_comparator_is_orthonormal_and_exact_at_r64():
+    # the exact DCT of the Sec. 3 comparison: C C^T = I; keeping all 64
+    # coefficients reproduces every image exactly (after rounding)
+    C = oracle.dct_matrix()
+    assert np.allclose(C @ C.T, np.eye(8), atol=1e-14)
+    assert np.allclose(C[0], np.sqrt(1 / 8)) and abs(C[1, 0] - 0.5 * math.cos(math.pi / 16)) < 1e-15
+    for img in (inputs.synth_image(64, 80, 21)[0], RNG.integers(0, 256, (32, 32), dtype=np.uint8)):
+        assert np.array_equal(oracle.dct_zonal(img, 64), img)
+
+
+def test_dct_comparator_dc_only_gives_block_means():
+    # r = 1 keeps the DC term only: each block becomes its (rounded) mean
+    img = inputs.synth_image(48, 64, 22)[0]
+    rec = oracle.dct_zonal(img, 1)
+    means = _blocks(img).mean(axis=(2, 3))
+    expect = np.rint(means)
+    got = _blocks(rec)
+    assert np.all(got == got[..., :1, :1])
+    assert np.array_equal(got[..., 0, 0], expect.astype(np.int64))
+
+
+def test_zonal_quality_improves_with_r():
+    # keeping more coefficients never hurts much: the proposed transform's
+    # error at r = 64 is zero, and the error falls as r grows (synthetic image)
+    img = inputs.synth_image(64, 64, 23)[0]
+    errs = [oracle.sse(oracle.roundtrip(img, oracle.MODE_ZONAL, None, r)[1], img) for r in (1, 6, 16, 45, 64)]
+    assert errs[-1] == 0 and errs[0] > errs[1] > errs[2] > errs[3]
