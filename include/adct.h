@@ -59,7 +59,7 @@ typedef enum {
 } adct_status;
 
 /* Quantiser modes (adct_quant.mode). */
-enum { ADCT_Q_NONE = 0, ADCT_Q_STEP = 1, ADCT_Q_ZONAL = 2, ADCT_Q_STEP_ZONAL = 3 };
+enum { ADCT_Q_NONE = 0, ADCT_Q_STEP = 1, ADCT_Q_ZONAL = 2, ADCT_Q_STEP_ZONAL = 3, ADCT_Q_ZONAL_ZZ = 4 };
 
 typedef struct adct_context adct_context;
 
@@ -72,6 +72,10 @@ typedef struct adct_context adct_context;
  *   dst   reconstructed pixels (may equal src)            (8-byte aligned)
  *   coef  int16 coefficients, block-major:  coef[((c * Hb + by) * Wb + bx) * 64 + i * 8 + j]
  *         with Hb = height/8, Wb = width/8, (i, j) = (row, column) frequency  (16-byte aligned)
+ *         With the quantiser mode ADCT_Q_ZONAL_ZZ coef is packed instead: r int16
+ *         per block, coef[((c * Hb + by) * Wb + bx) * r + t] = the coefficient at
+ *         zig-zag position t (t < r); only 2-byte alignment of the plane blocks
+ *         follows from this, the image's coef pointer stays 16-byte aligned.
  * A pointer an entry point does not use may be NULL.
  * Coefficient range: |Z_ij| <= 128 * 2^(a_i + a_j) <= 8192, so int16 is exact.
  */
@@ -90,7 +94,12 @@ typedef struct {
 /*
  * Quantiser.  mode: ADCT_Q_*.  Q: step table, row-major (i*8 + j), each entry in
  * [1, 65535] (used by STEP and STEP_ZONAL, ignored otherwise: Q = 1).
- * r: number of zig-zag coefficients kept, 0..64 (ZONAL and STEP_ZONAL).
+ * r: number of zig-zag coefficients kept, 0..64 (ZONAL, STEP_ZONAL, ZONAL_ZZ).
+ * ADCT_Q_ZONAL_ZZ is the ZONAL quantiser (q = Z at the first r zig-zag
+ * positions, 0 elsewhere) with the packed coefficient layout of adct_image:
+ * only the r kept values are stored, 2r bytes per block instead of 128.  It is
+ * written by the round trip entry points and read by adct_inverse;
+ * adct_quantise returns ADCT_ERR_UNSUPPORTED for it (the layouts differ).
  */
 typedef struct {
   int32_t mode;
@@ -300,7 +309,8 @@ adct_status adct_roundtrip_noalloc(const adct_image* imgs, int32_t n, const adct
  * adct_roundtrip / adct_inverse on the same inputs.
  *   encode: host pixels (width x height uint8, rows pitch bytes apart) are
  *           copied in, forward-transformed and quantised; the coefficients stay
- *           in the store under the handle reported by the completion.
+ *           in the store under the handle reported by the completion (2r bytes
+ *           per block with ADCT_Q_ZONAL_ZZ, 128 otherwise).
  *   decode: a stored handle is dequantised and inverted; the pixels are copied
  *           to host memory `out` (rows pitch bytes apart; width/height of the
  *           encoded image are returned).  The handle is pinned from submission

@@ -22,7 +22,7 @@ ADCT_ERR_UNSUPPORTED = 7
 ADCT_ERR_TOO_LARGE = 8
 NOALLOC_MAX_PLANES = 1024
 
-ADCT_Q_NONE, ADCT_Q_STEP, ADCT_Q_ZONAL, ADCT_Q_STEP_ZONAL = 0, 1, 2, 3
+ADCT_Q_NONE, ADCT_Q_STEP, ADCT_Q_ZONAL, ADCT_Q_STEP_ZONAL, ADCT_Q_ZONAL_ZZ = 0, 1, 2, 3, 4
 
 # Every symbol include/adct.h declares.
 EXPORTS = (

@@ -7,6 +7,7 @@ CUDA stream, and raises AdctError on a non-OK status.
 Tensor conventions (matching include/adct.h):
   pixels  uint8 [C, H, W] or [H, W], unit stride along W (rows and planes may be pitched)
   coef    int16 with C * H * W elements, contiguous; block-major [C, H/8, W/8, 8, 8]
+          (ADCT_Q_ZONAL_ZZ: packed, C * H/8 * W/8 * r elements, [C, H/8, W/8, r], zig-zag order)
   float   float32 [..., H, W] contiguous
 """
 from __future__ import annotations
@@ -17,7 +18,8 @@ from dataclasses import dataclass
 import torch
 
 from . import _native as N
-from ._native import ADCT_Q_NONE, ADCT_Q_STEP, ADCT_Q_STEP_ZONAL, ADCT_Q_ZONAL, AdctError  # noqa: F401
+from ._native import (ADCT_Q_NONE, ADCT_Q_STEP, ADCT_Q_STEP_ZONAL, ADCT_Q_ZONAL, ADCT_Q_ZONAL_ZZ,  # noqa: F401
+                      AdctError)
 
 
 def make_quant(mode: int, Q=None, r: int = 64) -> N.adct_quant:
@@ -33,6 +35,11 @@ def make_quant(mode: int, Q=None, r: int = 64) -> N.adct_quant:
             raise ValueError("Q entries must fit uint16")
         q.Q[k] = v
     return q
+
+
+def coef_per_block(quant) -> int:
+    """int16 coefficients stored per 8x8 block under `quant`: r for the packed zonal layout, else 64."""
+    return int(quant.r) if quant is not None and quant.mode == ADCT_Q_ZONAL_ZZ and 0 <= quant.r <= 64 else 64
 
 
 @dataclass
@@ -59,7 +66,7 @@ def _pix_geometry(t: torch.Tensor):
     raise ValueError("pixel tensors are [H, W] or [C, H, W]")
 
 
-def image_struct(im) -> N.adct_image:
+def image_struct(im, cpb: int = 64) -> N.adct_image:
     if isinstance(im, (tuple, list)):
         im = Image(*im)
     ref = im.src if im.src is not None else im.dst
@@ -71,16 +78,18 @@ def image_struct(im) -> N.adct_image:
             if g2 != (C, H, W, pitch, pstride):
                 raise ValueError("src and dst must share shape, pitch and plane stride")
     elif im.coef is not None:
-        # coefficient-only image: [C, H/8, W/8, 8, 8]
-        if im.coef.dim() != 5:
-            raise ValueError("a coefficient-only image needs coef shaped [C, H/8, W/8, 8, 8]")
+        # coefficient-only image: [C, H/8, W/8, 8, 8], or [C, H/8, W/8, r] packed
+        if im.coef.dim() != (5 if cpb == 64 else 4):
+            raise ValueError("a coefficient-only image needs coef shaped [C, H/8, W/8, 8, 8] "
+                             "([C, H/8, W/8, r] for the packed zonal layout)")
         C, hb, wb = im.coef.shape[:3]
         H, W, pitch, pstride = hb * 8, wb * 8, wb * 8, hb * 8 * wb * 8
     else:
         raise ValueError("image has no tensors")
     if im.coef is not None:
-        if im.coef.dtype != torch.int16 or not im.coef.is_contiguous() or im.coef.numel() != C * H * W:
-            raise ValueError("coef must be contiguous int16 with C*H*W elements")
+        if (im.coef.dtype != torch.int16 or not im.coef.is_contiguous()
+                or im.coef.numel() != C * (H // 8) * (W // 8) * cpb):
+            raise ValueError(f"coef must be contiguous int16 with {cpb} elements per 8x8 block")
     s.src = im.src.data_ptr() if im.src is not None else None
     s.dst = im.dst.data_ptr() if im.dst is not None else None
     s.coef = im.coef.data_ptr() if im.coef is not None else None
@@ -89,10 +98,11 @@ def image_struct(im) -> N.adct_image:
     return s
 
 
-def image_array(images):
+def image_array(images, quant=None):
+    cpb = coef_per_block(quant)
     arr = (N.adct_image * max(1, len(images)))()
     for k, im in enumerate(images):
-        arr[k] = image_struct(im)
+        arr[k] = image_struct(im, cpb)
     return arr
 
 
@@ -147,7 +157,7 @@ class Codec:
 
     # -- integer codec ------------------------------------------------------
     def _call(self, name, images, quant=None, stream=None):
-        arr = image_array(images)
+        arr = image_array(images, quant)
         args = [self.ctx, arr, len(images)]
         if quant is not None:
             args.append(ctypes.byref(quant))
@@ -167,7 +177,7 @@ class Codec:
         self._call("adct_roundtrip", images, quant, stream)
 
     def roundtrip_graph(self, images, quant, stream=None) -> bool:
-        arr = image_array(images)
+        arr = image_array(images, quant)
         rep = ctypes.c_int32(0)
         st = self.lib.adct_roundtrip_graph(self.ctx, arr, len(images), ctypes.byref(quant),
                                            _stream_handle(self.device, stream), ctypes.byref(rep))
@@ -184,7 +194,7 @@ class Codec:
         return {f: getattr(l, f) for f, _ in N.adct_launch._fields_}
 
     def autotune(self, images, quant, reps: int = 5, stream=None):
-        arr = image_array(images)
+        arr = image_array(images, quant)
         best = N.adct_launch()
         us = ctypes.c_float(0)
         st = self.lib.adct_autotune(self.ctx, arr, len(images), ctypes.byref(quant),
@@ -195,7 +205,7 @@ class Codec:
 
     def roundtrip_host(self, images, quant, chunk_bytes: int = 64 << 20):
         """End-to-end round trip on host (ideally pinned) tensors; synchronous."""
-        arr = image_array(images)
+        arr = image_array(images, quant)
         st = self.lib.adct_roundtrip_host(self.ctx, arr, len(images), ctypes.byref(quant), int(chunk_bytes))
         N.check(st, self.ctx, "adct_roundtrip_host")
 

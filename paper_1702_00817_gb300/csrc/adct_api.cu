@@ -142,7 +142,12 @@ void zigzag_rank(int rank[64]) {
 }
 
 bool uses_step(int mode) { return mode == ADCT_Q_STEP || mode == ADCT_Q_STEP_ZONAL; }
-bool uses_zonal(int mode) { return mode == ADCT_Q_ZONAL || mode == ADCT_Q_STEP_ZONAL; }
+bool uses_zonal(int mode) { return mode == ADCT_Q_ZONAL || mode == ADCT_Q_STEP_ZONAL || mode == ADCT_Q_ZONAL_ZZ; }
+
+// int16 coefficients stored per 8x8 block: r for the packed zonal layout, else 64.
+int32_t coef_per_block(const adct_quant* q) {
+  return (q && q->mode == ADCT_Q_ZONAL_ZZ && q->r >= 0 && q->r <= 64) ? q->r : 64;
+}
 
 // Per-position quantiser constants (see QuantParams).  pixel_input: Z is
 // computed from raw pixels, so Z_00 carries +8192 that the constants remove.
@@ -150,11 +155,12 @@ adct_status build_quant(adct_context* ctx, const adct_quant* q, bool pixel_input
   adct_quant none{};
   none.mode = ADCT_Q_NONE;
   if (!q) q = &none;
-  if (q->mode < ADCT_Q_NONE || q->mode > ADCT_Q_STEP_ZONAL) return fail(ctx, ADCT_ERR_INVALID_ARG, "bad quant mode");
+  if (q->mode < ADCT_Q_NONE || q->mode > ADCT_Q_ZONAL_ZZ) return fail(ctx, ADCT_ERR_INVALID_ARG, "bad quant mode");
   if (uses_zonal(q->mode) && (q->r < 0 || q->r > 64)) return fail(ctx, ADCT_ERR_INVALID_ARG, "r outside 0..64");
   int rank[64];
   zigzag_rank(rank);
   evenq = false;
+  qp.r = uses_zonal(q->mode) ? q->r : 64;
   for (int k = 0; k < 64; ++k) {
     const int i = k / 8, j = k % 8;
     const int shift = 6 - scale_exp(i) - scale_exp(j);
@@ -188,9 +194,10 @@ adct_status build_quant(adct_context* ctx, const adct_quant* q, bool pixel_input
 
 enum Need { NEED_SRC = 1, NEED_DST = 2, NEED_COEF = 4 };
 
-// Validates the images and builds the plane descriptor table.
+// Validates the images and builds the plane descriptor table; cpb is the
+// number of int16 coefficients stored per block (64, or r when packed).
 adct_status build_planes(adct_context* ctx, const adct_image* imgs, int32_t n, int need, std::vector<PlaneDesc>& planes,
-                         std::vector<int64_t>& starts) {
+                         std::vector<int64_t>& starts, int32_t cpb = 64) {
   if (n < 0) return fail(ctx, ADCT_ERR_INVALID_ARG, "negative image count");
   if (n > 0 && !imgs) return fail(ctx, ADCT_ERR_INVALID_ARG, "imgs is NULL");
   planes.clear();
@@ -217,7 +224,7 @@ adct_status build_planes(adct_context* ctx, const adct_image* imgs, int32_t n, i
       PlaneDesc d;
       d.src = im.src ? im.src + (int64_t)c * im.plane_stride : nullptr;
       d.dst = im.dst ? im.dst + (int64_t)c * im.plane_stride : nullptr;
-      d.coef = im.coef ? im.coef + (int64_t)c * nb * 64 : nullptr;
+      d.coef = im.coef ? im.coef + (int64_t)c * nb * cpb : nullptr;
       d.pitch = im.pitch;
       d.first = total;
       d.wb = wb;
@@ -331,9 +338,13 @@ adct_status run_codec(adct_context* ctx, const adct_image* imgs, int32_t n, cons
   st = build_quant(ctx, kind == K_FORWARD ? nullptr : quant, pixel_input, cl.qp, cl.evenq);
   if (st != ADCT_OK) return st;
   if (kind != K_FORWARD && kind != K_INVERSE) cl.qmode = quant->mode;
+  const bool packed = kind != K_FORWARD && quant->mode == ADCT_Q_ZONAL_ZZ;
+  if (packed && kind == K_QUANTISE)
+    return fail(ctx, ADCT_ERR_UNSUPPORTED, "the packed zonal layout is written by adct_roundtrip, not adct_quantise");
+  if (packed && kind == K_INVERSE) cl.qmode = QM_ZONAL_ZZ;
   std::vector<PlaneDesc> planes;
   std::vector<int64_t> starts;
-  st = build_planes(ctx, imgs, n, need_for_kind(kind), planes, starts);
+  st = build_planes(ctx, imgs, n, need_for_kind(kind), planes, starts, packed ? quant->r : 64);
   if (st != ADCT_OK) return st;
   cl.total = starts.back();
   if (cl.total == 0) return ADCT_OK;
@@ -665,7 +676,7 @@ adct_status adct_roundtrip_graph(adct_context* ctx, const adct_image* imgs, int3
   cl.qmode = quant->mode;
   std::vector<PlaneDesc> planes;
   std::vector<int64_t> starts;
-  st = build_planes(ctx, imgs, n, need_for_kind(kind), planes, starts);
+  st = build_planes(ctx, imgs, n, need_for_kind(kind), planes, starts, coef_per_block(quant));
   if (st != ADCT_OK) return st;
   cl.total = starts.back();
   if (cl.total == 0) return ADCT_OK;
@@ -804,14 +815,16 @@ adct_status adct_roundtrip_host(adct_context* ctx, const adct_image* himgs, int3
     acc += pix;
   }
   bounds.push_back(n);
-  size_t max_pix = 0;
+  size_t max_pix = 0, max_imgs = 0;
   for (size_t c = 0; c + 1 < bounds.size(); ++c) {
     size_t pix = 0;
     for (int32_t m = bounds[c]; m < bounds[c + 1]; ++m)
       pix += (size_t)himgs[m].width * himgs[m].height * himgs[m].channels;
     max_pix = std::max(max_pix, pix);
+    max_imgs = std::max(max_imgs, (size_t)(bounds[c + 1] - bounds[c]));
   }
   const bool want_coef = himgs[0].coef != nullptr, want_dst = himgs[0].dst != nullptr;
+  const int32_t cpb = coef_per_block(quant);
   for (auto& p : ctx->pipe) {
     if (!p.stream) ADCT_CUDA(ctx, cudaStreamCreateWithFlags(&p.stream, cudaStreamNonBlocking));
     const size_t pix_cap = (max_pix + 255) / 256 * 256;
@@ -827,16 +840,20 @@ adct_status adct_roundtrip_host(adct_context* ctx, const adct_image* himgs, int3
       }
       p.pix_cap = pix_cap;
     }
-    if (p.coef_cap < 2 * pix_cap) {
+    // coefficients: at most 128 bytes per 64 pixels, plus up to 16 bytes of
+    // alignment padding per image (the packed layout's images are not
+    // multiples of 16 bytes)
+    const size_t coef_cap = 2 * pix_cap + 16 * max_imgs;
+    if (p.coef_cap < coef_cap) {
       cudaStreamSynchronize(p.stream);
       if (p.coef) cudaFree(p.coef);
       p.coef = nullptr;
       p.coef_cap = 0;
-      if (cudaMalloc(&p.coef, 2 * pix_cap) != cudaSuccess) {
+      if (cudaMalloc(&p.coef, coef_cap) != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, ADCT_ERR_OOM, "pipeline staging cudaMalloc failed");
       }
-      p.coef_cap = 2 * pix_cap;
+      p.coef_cap = coef_cap;
     }
   }
   // 1D copies of contiguous images are merged with their neighbours when both
@@ -863,7 +880,7 @@ adct_status adct_roundtrip_host(adct_context* ctx, const adct_image* himgs, int3
     h2d.clear();
     d2h_coef.clear();
     d2h_pix.clear();
-    size_t off = 0;
+    size_t off = 0, coff = 0;  // pixel and coefficient offsets into the staging buffers
     for (int32_t m = bounds[c]; m < bounds[c + 1]; ++m) {
       const adct_image& h = himgs[m];
       const size_t plane = (size_t)h.width * h.height;
@@ -871,7 +888,7 @@ adct_status adct_roundtrip_host(adct_context* ctx, const adct_image* himgs, int3
       adct_image d{};
       d.src = p.src + off;
       d.dst = want_dst ? p.dst + off : nullptr;
-      d.coef = want_coef ? p.coef + off : nullptr;  // 64 int16 per 64 pixels: same element offset
+      d.coef = want_coef ? p.coef + coff : nullptr;
       d.width = h.width;
       d.height = h.height;
       d.channels = h.channels;
@@ -884,12 +901,13 @@ adct_status adct_roundtrip_host(adct_context* ctx, const adct_image* himgs, int3
           ADCT_CUDA(ctx, cudaMemcpy2DAsync(p.src + off + ch * plane, h.width, h.src + (int64_t)ch * h.plane_stride,
                                            h.pitch, h.width, h.height, cudaMemcpyHostToDevice, s));
       }
-      if (want_coef) add_run(d2h_coef, h.coef, d.coef, plane * h.channels * sizeof(int16_t));
+      if (want_coef) add_run(d2h_coef, h.coef, d.coef, plane / 64 * cpb * h.channels * sizeof(int16_t));
       if (want_dst) {
         if (packed) add_run(d2h_pix, h.dst, d.dst, plane * h.channels);
       }
       dimgs.push_back(d);
       off += plane * h.channels;
+      coff += (plane / 64 * cpb * h.channels + 7) / 8 * 8;  // cpb int16 per block; 16-byte aligned images
     }
     for (const Run& r : h2d) ADCT_CUDA(ctx, cudaMemcpyAsync(r.dst, r.src, r.bytes, cudaMemcpyHostToDevice, s));
     adct_status st = run_codec(ctx, dimgs.data(), (int32_t)dimgs.size(), quant, kind, s, ctx->shape);
@@ -1060,7 +1078,7 @@ extern "C" adct_status adct_roundtrip_noalloc(const adct_image* imgs, int32_t n,
       PlaneDesc& d = table.planes[np];
       d.src = im.src + (int64_t)c * im.plane_stride;
       d.dst = im.dst ? im.dst + (int64_t)c * im.plane_stride : nullptr;
-      d.coef = im.coef ? im.coef + (int64_t)c * nb * 64 : nullptr;
+      d.coef = im.coef ? im.coef + (int64_t)c * nb * coef_per_block(quant) : nullptr;
       d.pitch = im.pitch;
       d.first = total;
       d.wb = wb;

@@ -114,6 +114,11 @@ __device__ __forceinline__ int16_t* coef_of(const PlaneDesc* d, const Pos& q) {
   return (int16_t*)c + ((int64_t)q.by * __ldg(&d->wb) + q.bx) * 64;
 }
 
+__device__ __forceinline__ int16_t* coef_of_zz(const PlaneDesc* d, const Pos& q, int r) {
+  const int16_t* c = (const int16_t*)__ldg((const unsigned long long*)&d->coef);
+  return (int16_t*)c + ((int64_t)q.by * __ldg(&d->wb) + q.bx) * r;
+}
+
 // Plane cursor of one lane: the flat index only grows (by 32 per tile), so the
 // plane index only moves forward and (by, bx) advance incrementally; a
 // division by the plane's width is needed only when a tile crosses a block
@@ -193,6 +198,18 @@ __device__ __forceinline__ uint32_t block_step(const uint8_t* __restrict__ in, u
       }
     }
     fwd2d(v);  // Z + 8192 e0 e0^T (raw pixels; the level shift lives in the constants)
+  } else if (QMODE == QM_ZONAL_ZZ) {
+    // packed input: the first r zig-zag coefficients of this block
+    constexpr ZigZag zz = make_zigzag();
+    const int16_t* c = (const int16_t*)__ldg((const unsigned long long*)&d->coef) +
+                       ((int64_t)pos.by * __ldg(&d->wb) + pos.bx) * qp.r;
+#pragma unroll
+    for (int k = 0; k < 64; ++k) v[k] = 0;
+#pragma unroll
+    for (int t = 0; t < 64; ++t) {
+      if (t >= qp.r) break;
+      v[zz.pos[t]] = (int32_t)__ldg(c + t);
+    }
   } else {
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
@@ -201,6 +218,20 @@ __device__ __forceinline__ uint32_t block_step(const uint8_t* __restrict__ in, u
       v[8 * t + 2] = sext_lo16(u.y); v[8 * t + 3] = sext_hi16(u.y);
       v[8 * t + 4] = sext_lo16(u.z); v[8 * t + 5] = sext_hi16(u.z);
       v[8 * t + 6] = sext_lo16(u.w); v[8 * t + 7] = sext_hi16(u.w);
+    }
+  }
+
+  // ---- packed zonal output: the first r zig-zag coefficients, staged per lane ----
+  if (QMODE == QM_ZONAL_ZZ && KT::write_coef) {
+    constexpr ZigZag zz = make_zigzag();
+    int16_t* st16 = (int16_t*)stage_out + lane * qp.r;
+#pragma unroll
+    for (int t = 0; t < 64; ++t) {
+      if (t >= qp.r) break;
+      const int k = zz.pos[t];
+      const int32_t zq = v[k] + ((KT::in_pix && k == 0) ? -8192 : 0);  // the true coefficient
+      if (stage_coef) st16[t] = (int16_t)zq;
+      else coef_of_zz(d, pos, qp.r)[t] = (int16_t)zq;
     }
   }
 
@@ -221,6 +252,8 @@ __device__ __forceinline__ uint32_t block_step(const uint8_t* __restrict__ in, u
       if (KIND == K_INVERSE) {
         q[j] = z;
         v[k] = (int32_t)((uint32_t)z * (uint32_t)qp.w[k] + (uint32_t)bias);
+      } else if (QMODE == QM_ZONAL_ZZ) {
+        v[k] = (int32_t)((uint32_t)((z + zoff) & qp.keep[k]) * (uint32_t)qp.w[k] + (uint32_t)bias);
       } else if (QMODE == QM_STEP || QMODE == QM_STEP_ZONAL) {
         int32_t n = z + qp.c[k];
         if (EVENQ) n += ((z + zoff) >> 31) & qp.sflag[k];
@@ -238,7 +271,7 @@ __device__ __forceinline__ uint32_t block_step(const uint8_t* __restrict__ in, u
         if (KT::inv) v[k] = (int32_t)((uint32_t)qq * (uint32_t)qp.w[k] + (uint32_t)bias);
       }
     }
-    if (KT::write_coef) {
+    if (KT::write_coef && QMODE != QM_ZONAL_ZZ) {
       int4 u;
       u.x = (int)pack16(q[0], q[1]);
       u.y = (int)pack16(q[2], q[3]);
@@ -311,6 +344,32 @@ __device__ __forceinline__ void write_back(const uint8_t* __restrict__ stage_out
   }
 }
 
+// Write a staged 32-block half-tile of packed zonal coefficients (r int16 per
+// block, lane l's at [l r, l r + r)) back to memory.  When every active lane is
+// in lane 0's plane the half-tile is one contiguous range of 32 r values,
+// written as 4-byte words when aligned; otherwise each lane writes its own r.
+__device__ __forceinline__ void write_back_zz(const uint8_t* __restrict__ stage_out,
+                                             const PlaneDesc* __restrict__ planes, const Pos& pos, int lane, int r) {
+  const bool active = pos.plane >= 0;
+  const int plane0 = __shfl_sync(0xffffffffu, pos.plane, 0);
+  const unsigned act = __ballot_sync(0xffffffffu, active);
+  int16_t* mine = active ? coef_of_zz(planes + pos.plane, pos, r) : nullptr;
+  const int16_t* st16 = (const int16_t*)stage_out;
+  if (__all_sync(0xffffffffu, !active || pos.plane == plane0)) {
+    int16_t* base = (int16_t*)__shfl_sync(0xffffffffu, (unsigned long long)mine, 0);
+    const int n = __popc(act) * r;  // values to write
+    if (((uintptr_t)base & 3) == 0 && (n & 1) == 0) {
+      uint32_t* gw = (uint32_t*)base;
+      const uint32_t* sw = (const uint32_t*)st16;
+      for (int k = lane; k < n / 2; k += 32) __stcs(gw + k, sw[k]);
+    } else {
+      for (int k = lane; k < n; k += 32) base[k] = st16[k];
+    }
+  } else if (active) {
+    for (int t = 0; t < r; ++t) mine[t] = st16[lane * r + t];
+  }
+}
+
 template <int KIND, int QMODE, bool EVENQ>
 __global__ void __launch_bounds__(kMaxThreads, 3)
 k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts, int32_t nplanes, int64_t total,
@@ -356,7 +415,7 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
 #pragma unroll
           for (int i = 0; i < 8; ++i) cp_async8(sa + (i * 32 + lane) * 8, src + i * pitch);
         }
-      } else {
+      } else if (QMODE != QM_ZONAL_ZZ) {
         // Coefficients: lane copies 16-byte chunk c of block b (512 contiguous
         // bytes per warp instruction when the tile lies in one plane).
         const int16_t* mine = q[u].plane >= 0 ? coef_of(planes + q[u].plane, q[u]) : nullptr;
@@ -407,7 +466,10 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
     if (KT::write_coef && stage_coef) {
       __syncwarp();
 #pragma unroll
-      for (int u = 0; u < kBpl; ++u) write_back(stage_out + u * kTileBytesOut, planes, pc[u], lane);
+      for (int u = 0; u < kBpl; ++u) {
+        if (QMODE == QM_ZONAL_ZZ) write_back_zz(stage_out + u * kTileBytesOut, planes, pc[u], lane, qp.r);
+        else write_back(stage_out + u * kTileBytesOut, planes, pc[u], lane);
+      }
       __syncwarp();
     }
 #pragma unroll
@@ -423,6 +485,8 @@ using KernelFn = void (*)(const PlaneDesc*, const int64_t*, int32_t, int64_t, in
 template <int KIND, bool EVENQ>
 KernelFn pick_mode(int qmode) {
   switch (qmode) {
+    case QM_ZONAL_ZZ: return (KIND == K_RT_FULL || KIND == K_RT_COEF) ? k_codec<KIND, QM_ZONAL_ZZ, false>
+                                                                     : k_codec<KIND, QM_ZONAL, false>;
     case QM_STEP: return k_codec<KIND, QM_STEP, EVENQ>;
     case QM_ZONAL: return k_codec<KIND, QM_ZONAL, false>;
     case QM_STEP_ZONAL: return k_codec<KIND, QM_STEP_ZONAL, EVENQ>;
@@ -441,7 +505,7 @@ KernelFn pick_kernel_q(int kind, int qmode) {
         case QM_STEP_ZONAL: return k_codec<K_QUANTISE, QM_STEP_ZONAL, EVENQ>;
         default: return nullptr;
       }
-    case K_INVERSE: return k_codec<K_INVERSE, QM_NONE, false>;
+    case K_INVERSE: return qmode == QM_ZONAL_ZZ ? k_codec<K_INVERSE, QM_ZONAL_ZZ, false> : k_codec<K_INVERSE, QM_NONE, false>;
     case K_RT_FULL: return pick_mode<K_RT_FULL, EVENQ>(qmode);
     case K_RT_PIX: return pick_mode<K_RT_PIX, EVENQ>(qmode);
     case K_RT_COEF: return pick_mode<K_RT_COEF, EVENQ>(qmode);

@@ -137,8 +137,31 @@ struct QuantParams {
   int32_t w[64];
   int32_t kw[64];
   int32_t keep[64];
+  int32_t r;  // zonal: number of zig-zag coefficients kept (the packed layout stores r per block)
 };
 
-enum QMode { QM_NONE = 0, QM_STEP = 1, QM_ZONAL = 2, QM_STEP_ZONAL = 3 };
+// QM_ZONAL_ZZ: the zonal quantiser with coefficients stored packed, the first
+// r zig-zag coefficients of each block (r int16 per block) instead of 64.
+enum QMode { QM_NONE = 0, QM_STEP = 1, QM_ZONAL = 2, QM_STEP_ZONAL = 3, QM_ZONAL_ZZ = 4 };
+
+// The standard zig-zag sequence over an 8x8 block (Sec. 3): pos[t] = 8 i + j of
+// the t-th coefficient; anti-diagonals s = i + j in order, even s walked with i
+// decreasing, odd s with i increasing.
+struct ZigZag {
+  int pos[64];
+};
+__host__ __device__ constexpr ZigZag make_zigzag() {
+  ZigZag z{};
+  int t = 0;
+  for (int s = 0; s < 15; ++s) {
+    const int lo = s < 8 ? 0 : s - 7, hi = s < 8 ? s : 7;
+    if (s % 2 == 0) {
+      for (int i = hi; i >= lo; --i) z.pos[t++] = 8 * i + (s - i);
+    } else {
+      for (int i = lo; i <= hi; ++i) z.pos[t++] = 8 * i + (s - i);
+    }
+  }
+  return z;
+}
 
 }  // namespace adct

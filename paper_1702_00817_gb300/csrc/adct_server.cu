@@ -15,6 +15,7 @@
 // and their work overlaps on the device.  Clients poll completions.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -128,6 +129,7 @@ struct adct_server {
   int device = 0;
   adct_context* ctx = nullptr;
   adct_quant quant{};
+  int32_t cpb = 64;  // int16 coefficients stored per block (r for the packed zonal layout)
   int32_t max_batch = 256;
   Arena arena;
   std::vector<cudaStream_t> streams;
@@ -251,7 +253,8 @@ void admit(adct_server* s, std::vector<Req>& enc, std::vector<Req>& dec) {
       }
       if (!it->second.ready) break;  // its encode is still running: keep FIFO order
     }
-    const size_t need = (r.kind == KIND_ENCODE) ? 3 * pix : pix;
+    const size_t cbytes = std::max<size_t>(pix / 64 * (size_t)s->cpb * 2, 16);  // the stored coefficients
+    const size_t need = (r.kind == KIND_ENCODE) ? pix + cbytes : pix;
     if (need + 2 * kAlign > s->arena.bytes()) {
       Req big = r;
       s->queue.pop_front();
@@ -260,10 +263,10 @@ void admit(adct_server* s, std::vector<Req>& enc, std::vector<Req>& dec) {
       continue;
     }
     size_t off_tmp = s->arena.alloc(pix), off_coef = SIZE_MAX;
-    if (off_tmp != SIZE_MAX && r.kind == KIND_ENCODE) off_coef = s->arena.alloc(2 * pix);
+    if (off_tmp != SIZE_MAX && r.kind == KIND_ENCODE) off_coef = s->arena.alloc(cbytes);
     while ((off_tmp == SIZE_MAX || (r.kind == KIND_ENCODE && off_coef == SIZE_MAX)) && evict_one(s)) {
       if (off_tmp == SIZE_MAX) off_tmp = s->arena.alloc(pix);
-      if (off_tmp != SIZE_MAX && r.kind == KIND_ENCODE && off_coef == SIZE_MAX) off_coef = s->arena.alloc(2 * pix);
+      if (off_tmp != SIZE_MAX && r.kind == KIND_ENCODE && off_coef == SIZE_MAX) off_coef = s->arena.alloc(cbytes);
     }
     if (off_tmp == SIZE_MAX || (r.kind == KIND_ENCODE && off_coef == SIZE_MAX)) {
       if (off_tmp != SIZE_MAX) s->arena.free(off_tmp, pix);
@@ -276,7 +279,7 @@ void admit(adct_server* s, std::vector<Req>& enc, std::vector<Req>& dec) {
     a.tmp_bytes = pix;
     if (a.kind == KIND_ENCODE) {
       a.handle = s->next_handle++;
-      Entry e{off_coef, 2 * pix, a.width, a.height, 0, s->tick, false};
+      Entry e{off_coef, cbytes, a.width, a.height, 0, s->tick, false};
       s->store[a.handle] = e;
       s->lru[s->tick++] = a.handle;
       enc.push_back(a);
@@ -402,6 +405,7 @@ adct_status adct_server_create(adct_server** out, int32_t device, const adct_ser
   adct_server* s = new adct_server();
   s->device = device;
   s->quant = cfg->quant;
+  if (s->quant.mode == ADCT_Q_ZONAL_ZZ && s->quant.r >= 0 && s->quant.r <= 64) s->cpb = s->quant.r;
   s->max_batch = cfg->max_batch > 0 ? cfg->max_batch : 256;
   const int64_t budget = cfg->budget_bytes > 0 ? cfg->budget_bytes : (4ll << 30);
   const int nstreams = cfg->streams > 0 ? cfg->streams : 4;

@@ -27,7 +27,7 @@ from dataclasses import dataclass, field
 
 import torch
 
-from .codec import ADCT_Q_STEP, Codec, Image, make_quant
+from .codec import ADCT_Q_STEP, Codec, Image, coef_per_block, make_quant
 
 
 @dataclass
@@ -149,7 +149,7 @@ class Server:
     def _need_bytes(self, r: Request) -> int:
         if r.kind == "encode":
             H, W = r.pixels.shape
-            return 3 * H * W  # pixels + int16 coefficients
+            return H * W + (H // 8) * (W // 8) * coef_per_block(self.quant) * 2  # pixels + int16 coefficients
         e = self.store.get(r.handle)
         return 0 if e is None else e["h"] * e["w"]  # output pixels
 
@@ -235,7 +235,9 @@ class Server:
                         H, W = r.pixels.shape
                         px = torch.empty((H, W), dtype=torch.uint8, device=self.dev)
                         px.copy_(r.pixels, non_blocking=True)
-                        coef = torch.empty((1, H // 8, W // 8, 8, 8), dtype=torch.int16, device=self.dev)
+                        cpb = coef_per_block(self.quant)
+                        shape = (1, H // 8, W // 8, 8, 8) if cpb == 64 else (1, H // 8, W // 8, cpb)
+                        coef = torch.empty(shape, dtype=torch.int16, device=self.dev)
                         r._dev = [px, coef]
                         r.result = next(self._handles)
                         imgs.append(Image(px, None, coef))
