@@ -56,7 +56,7 @@ struct PipeSlot {
 struct adct_context {
   int device = 0;
   int sm_count = 0;
-  LaunchShape shape{128, 3, 1};
+  LaunchShape shape{128, 0, 1};  // ctas_per_sm 0: chosen per kernel kind
   std::string last_error;
   Slot slots[kSlots];
   int next_slot = 0;
@@ -295,7 +295,7 @@ adct_status acquire_slot(adct_context* ctx, size_t bytes, Slot** out) {
 }
 
 adct_status check_shape(adct_context* ctx, const LaunchShape& sh) {
-  if (sh.threads < 32 || sh.threads > 128 || sh.threads % 32 || sh.ctas_per_sm < 1 || sh.ctas_per_sm > 32 ||
+  if (sh.threads < 32 || sh.threads > 128 || sh.threads % 32 || sh.ctas_per_sm < 0 || sh.ctas_per_sm > 32 ||
       (sh.stage_coef != 0 && sh.stage_coef != 1))
     return fail(ctx, ADCT_ERR_INVALID_ARG, "launch shape out of range");
   return ADCT_OK;
@@ -508,7 +508,7 @@ adct_status adct_set_launch(adct_context* ctx, const adct_launch* l) {
   LaunchShape sh = ctx->shape;
   if (l->reserved) return fail(ctx, ADCT_ERR_INVALID_ARG, "reserved must be 0");
   if (l->threads_per_cta) sh.threads = l->threads_per_cta;
-  if (l->ctas_per_sm) sh.ctas_per_sm = l->ctas_per_sm;
+  if (l->ctas_per_sm) sh.ctas_per_sm = l->ctas_per_sm < 0 ? 0 : l->ctas_per_sm;
   sh.stage_coef = l->stage_coef;
   adct_status st = check_shape(ctx, sh);
   if (st != ADCT_OK) return st;
@@ -1113,7 +1113,7 @@ extern "C" adct_status adct_roundtrip_noalloc(const adct_image* imgs, int32_t n,
   cl.starts = (const int64_t*)((char*)scratch + plane_bytes);
   cl.nplanes = np;
   cl.total = total;
-  const LaunchShape shape{128, 3, 1};
+  const LaunchShape shape{128, 0, 1};
   if (launch_codec(cl, shape, sm_count, s) != cudaSuccess) {
     cudaGetLastError();
     return ADCT_ERR_CUDA;

@@ -1,511 +1,39 @@
-// Integer codec kernels for sm_103a: the blockwise 2D 14-addition transform
-// (Sec. 2 fast algorithm T = P A3 A2 A1; Sec. 3 8x8 blocks), the D^2-merged
-// quantiser and the inverse, as one persistent kernel over a flattened block
-// index.  The path is add-only and bound by HBM bytes, so no tensor cores.
-//
-// Work split.  The grid is sized to the SMs; each warp owns a contiguous
-// chunk of the flat block index and walks it in tiles of 32 blocks, one 8x8
-// block per lane.  An 8x8 block lives in 64 registers, so both passes of the
-// separable transform and the transpose between them are register renaming.
-//
-// Memory pipeline per warp (all in the warp's slice of shared memory):
-//   - the next tile's input is prefetched with cp.async while the current one
-//     is computed (pixels: each lane copies its block's 8 rows, 8 bytes each,
-//     so one copy instruction of the warp moves 256 contiguous bytes;
-//     coefficients: the warp copies the tile's contiguous 4 KB, 512 bytes per
-//     instruction, into a 16-byte-chunk XOR swizzle);
-//   - quantised coefficients of a full tile are staged in the same swizzle and
-//     written back as 512-byte contiguous warp stores (one L2 request per
-//     128-byte line instead of one per 16 bytes);
-//   - reconstructed pixels are stored directly (256 contiguous bytes per warp
-//     instruction already).
-//
-// Arithmetic per block (one lane):
-//   forward  raw bytes -> 8 row butterflies -> 8 column butterflies (Z + 8192 e0e0^T);
-//   quantise n = Z + c (bias, offset and level shift folded into one constant,
-//            added by the last butterfly stage), m = umulhi(n, magic) = floor(n / Q),
-//            q = m - K; for tables with even steps the sign of Z moves the bias by
-//            one so that ties round away from zero;
-//   dequant  S = q w, w = Q 2^(6 - a_i - a_j) (D^2 merged), + 8224 at (0, 0)
-//            (rounding and level shift of every pixel: T^T e0 = 1);
-//   inverse  8 column then 8 row transposed butterflies;
-//   output   pixel = saturate_u8(R >> 6).
-#include <cuda_runtime.h>
-
-#include "adct_internal.h"
+// Instantiation and launch of the integer codec kernel (the kernel itself is
+// in adct_codec_kernel.cuh): every kind and quantiser mode with the full zone,
+// plus the dispatch to the zone-specialised zonal kernels.
+#include "adct_codec_kernel.cuh"
 
 namespace adct {
 namespace {
 
-constexpr int kMaxThreads = 128;  // with 3 CTAs per SM: up to 168 registers per thread
-constexpr int kTileBytesOut = 4096;  // output staging: 32 blocks of int16 coefficients
-
-__device__ __forceinline__ int32_t sext_lo16(uint32_t w) { return (int32_t)(int16_t)(w & 0xFFFFu); }
-__device__ __forceinline__ int32_t sext_hi16(uint32_t w) { return ((int32_t)w) >> 16; }
-__device__ __forceinline__ uint32_t pack16(int32_t lo, int32_t hi) {
-  return __byte_perm((uint32_t)lo, (uint32_t)hi, 0x5410);
-}
-// (c << 16) | (sat_u8(a) << 8) | sat_u8(b)
-__device__ __forceinline__ uint32_t cvt_pack_u8(int32_t a, int32_t b, uint32_t c) {
-  uint32_t d;
-  asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-  return d;
-}
-// four reconstructed values (R + 8224) -> four saturated pixels, p0 in the lowest byte
-__device__ __forceinline__ uint32_t pixels4(int32_t r0, int32_t r1, int32_t r2, int32_t r3) {
-  const uint32_t hi = cvt_pack_u8(r3 >> 6, r2 >> 6, 0u);
-  return cvt_pack_u8(r1 >> 6, r0 >> 6, hi);
-}
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// 16-byte chunk c of block b inside a 32-block coefficient tile, XOR-swizzled
-// so that 8 consecutive lanes touching one chunk each hit distinct banks.
-__device__ __forceinline__ int swz(int b, int c) { return b * 128 + ((c ^ (b & 7)) << 4); }
-
-// Reconstruction offset carried by S_00: 32 (rounding of R / 64) + 128 * 64
-// (level shift); T^T e0 = 1 spreads it to every pixel of the block.
-constexpr int32_t kDcBias = 32 + 128 * 64;
-
-template <int KIND>
-struct KindTraits {
-  static constexpr bool in_pix =
-      (KIND == K_FORWARD || KIND == K_RT_FULL || KIND == K_RT_PIX || KIND == K_RT_COEF || KIND == K_RT_SSE);
-  static constexpr bool quant =
-      (KIND == K_QUANTISE || KIND == K_RT_FULL || KIND == K_RT_PIX || KIND == K_RT_COEF || KIND == K_RT_SSE);
-  static constexpr bool write_coef = (KIND == K_FORWARD || KIND == K_QUANTISE || KIND == K_RT_FULL || KIND == K_RT_COEF);
-  static constexpr bool inv = (KIND == K_INVERSE || KIND == K_RT_FULL || KIND == K_RT_PIX || KIND == K_RT_SSE);
-  static constexpr bool sse = (KIND == K_RT_SSE);  // compare with the input instead of storing pixels
-};
-
-// Position of one lane's block: plane index and block coordinates (by, bx);
-// plane < 0 past the end of the warp's chunk.  Addresses are recomputed from
-// the plane descriptor (an L1 hit) when needed, which keeps the per-lane state
-// of the two tiles in flight to six registers.
-struct Pos {
-  int plane;
-  uint32_t by, bx;
-};
-
-__device__ __forceinline__ int64_t pix_off(const PlaneDesc* d, const Pos& q) {
-  return (int64_t)(8 * q.by) * __ldg(&d->pitch) + 8 * q.bx;
-}
-__device__ __forceinline__ const uint8_t* src_of(const PlaneDesc* d) {
-  return (const uint8_t*)__ldg((const unsigned long long*)&d->src);
-}
-__device__ __forceinline__ uint8_t* dst_of(const PlaneDesc* d) {
-  return (uint8_t*)__ldg((const unsigned long long*)&d->dst);
-}
-__device__ __forceinline__ int16_t* coef_of(const PlaneDesc* d, const Pos& q) {
-  const int16_t* c = (const int16_t*)__ldg((const unsigned long long*)&d->coef);
-  return (int16_t*)c + ((int64_t)q.by * __ldg(&d->wb) + q.bx) * 64;
-}
-
-__device__ __forceinline__ int16_t* coef_of_zz(const PlaneDesc* d, const Pos& q, int r) {
-  const int16_t* c = (const int16_t*)__ldg((const unsigned long long*)&d->coef);
-  return (int16_t*)c + ((int64_t)q.by * __ldg(&d->wb) + q.bx) * r;
-}
-
-// Plane cursor of one lane: the flat index only grows (by 32 per tile), so the
-// plane index only moves forward and (by, bx) advance incrementally; a
-// division by the plane's width is needed only when a tile crosses a block
-// row.  Offsets are 32-bit, relative to the warp's chunk start.
-struct Cursor {
-  int p;
-  int32_t first, next_start;  // plane p spans [first, next_start) relative to the chunk start
-  Pos last;                   // position returned by the previous call (plane < 0: none)
-
-  __device__ __forceinline__ Pos locate(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts,
-                                        int64_t begin, int32_t r, int32_t rend) {
-    Pos q;
-    if (r >= rend) {
-      q.plane = -1; q.by = 0; q.bx = 0;
-      last = q;
-      return q;
-    }
-    bool moved = false;
-    if (r >= next_start) {
-      do {
-        ++p;
-        next_start = (int32_t)min(__ldg(starts + p + 1) - begin, (int64_t)0x7fffffff);
-      } while (r >= next_start);
-      first = (int32_t)(__ldg(starts + p) - begin);
-      moved = true;
-    }
-    const uint32_t wb = (uint32_t)__ldg(&planes[p].wb);
-    if (!moved && last.plane == p && last.bx + 32 < wb) {  // same block row, 32 blocks further
-      q = last;
-      q.bx += 32;
-    } else {
-      const uint32_t f = (uint32_t)(r - first);
-      q.plane = p;
-      q.by = f / wb;
-      q.bx = f - q.by * wb;
-    }
-    last = q;
-    return q;
-  }
-};
-
-// Blocks per lane per tile: a warp walks its chunk in tiles of 32 * kBpl
-// blocks, lane l owning blocks l, l + 32, ...  One block per lane measured
-// best: two per lane left the instruction count per block unchanged (the
-// overhead is per block, not per tile) and doubled the shared memory per CTA,
-// which ran slower.
-constexpr int kBpl = 1;
-
-// Per-warp shared memory for kind KIND: two input stages and one output stage.
-template <int KIND>
-struct SmemPlan {
-  static constexpr int in_per32 = KindTraits<KIND>::in_pix ? 2048 : 4096;  // one 32-block tile of input
-  static constexpr int in_stage = kBpl * in_per32;
-  static constexpr int out_stage = KindTraits<KIND>::write_coef ? kBpl * kTileBytesOut : 0;
-  static constexpr int warp = 2 * in_stage + out_stage;
-};
-
-// Arithmetic of one 8x8 block: read its input from the input stage, quantise,
-// stage or store q, dequantise, invert and store the pixels.
-template <int KIND, int QMODE, bool EVENQ>
-__device__ __forceinline__ uint32_t block_step(const uint8_t* __restrict__ in, uint8_t* __restrict__ stage_out,
-                                               const PlaneDesc* __restrict__ planes, const Pos& pos, int stage_coef,
-                                               const QuantParams& qp, int lane) {
-  using KT = KindTraits<KIND>;
-  if (pos.plane < 0) return 0;
-  const PlaneDesc* d = planes + pos.plane;
-  int32_t v[64];
-  if (KT::in_pix) {
-    const uint2* st = (const uint2*)in;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const uint2 w = st[i * 32 + lane];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        v[8 * i + j] = (int32_t)__byte_perm(w.x, 0u, 0x4440 | j);
-        v[8 * i + 4 + j] = (int32_t)__byte_perm(w.y, 0u, 0x4440 | j);
-      }
-    }
-    fwd2d(v);  // Z + 8192 e0 e0^T (raw pixels; the level shift lives in the constants)
-  } else if (QMODE == QM_ZONAL_ZZ) {
-    // packed input: the first r zig-zag coefficients of this block
-    constexpr ZigZag zz = make_zigzag();
-    const int16_t* c = (const int16_t*)__ldg((const unsigned long long*)&d->coef) +
-                       ((int64_t)pos.by * __ldg(&d->wb) + pos.bx) * qp.r;
-#pragma unroll
-    for (int k = 0; k < 64; ++k) v[k] = 0;
-#pragma unroll
-    for (int t = 0; t < 64; ++t) {
-      if (t >= qp.r) break;
-      v[zz.pos[t]] = (int32_t)__ldg(c + t);
-    }
-  } else {
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      const int4 u = *(const int4*)(in + swz(lane, t));
-      v[8 * t + 0] = sext_lo16(u.x); v[8 * t + 1] = sext_hi16(u.x);
-      v[8 * t + 2] = sext_lo16(u.y); v[8 * t + 3] = sext_hi16(u.y);
-      v[8 * t + 4] = sext_lo16(u.z); v[8 * t + 5] = sext_hi16(u.z);
-      v[8 * t + 6] = sext_lo16(u.w); v[8 * t + 7] = sext_hi16(u.w);
-    }
-  }
-
-  // ---- packed zonal output: the first r zig-zag coefficients, staged per lane ----
-  if (QMODE == QM_ZONAL_ZZ && KT::write_coef) {
-    constexpr ZigZag zz = make_zigzag();
-    int16_t* st16 = (int16_t*)stage_out + lane * qp.r;
-#pragma unroll
-    for (int t = 0; t < 64; ++t) {
-      if (t >= qp.r) break;
-      const int k = zz.pos[t];
-      const int32_t zq = v[k] + ((KT::in_pix && k == 0) ? -8192 : 0);  // the true coefficient
-      if (stage_coef) st16[t] = (int16_t)zq;
-      else coef_of_zz(d, pos, qp.r)[t] = (int16_t)zq;
-    }
-  }
-
-  // ---- quantise (q, stored row by row) and dequantise in place (v <- S) ----
-  // S = q * w with w = Q 2^(6 - a_i - a_j) (D^2 merged), plus kDcBias at
-  // (0, 0).  For STEP it is formed from m directly (S = m * w + kw, kw =
-  // -K * w (+ kDcBias)), independent of the q = m - K that goes to memory.
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    int32_t q[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int k = 8 * i + j;
-      const int32_t bias = (k == 0) ? kDcBias : 0;
-      const int32_t z = v[k];  // raw: Z + 8192 at (0, 0) when the input was pixels
-      // T (X - 128) T^T = T X T^T - 8192 e0 e0^T  (T 1 = 8 e0)
-      const int32_t zoff = (KT::in_pix && k == 0) ? -8192 : 0;
-      if (KIND == K_INVERSE) {
-        q[j] = z;
-        v[k] = (int32_t)((uint32_t)z * (uint32_t)qp.w[k] + (uint32_t)bias);
-      } else if (QMODE == QM_ZONAL_ZZ) {
-        v[k] = (int32_t)((uint32_t)((z + zoff) & qp.keep[k]) * (uint32_t)qp.w[k] + (uint32_t)bias);
-      } else if (QMODE == QM_STEP || QMODE == QM_STEP_ZONAL) {
-        int32_t n = z + qp.c[k];
-        if (EVENQ) n += ((z + zoff) >> 31) & qp.sflag[k];
-        const uint32_t m = __umulhi((uint32_t)n, qp.magic[k]);
-        int32_t qq = (int32_t)m - qp.K[k];
-        if (QMODE == QM_STEP_ZONAL) qq &= qp.keep[k];
-        q[j] = qq;
-        if (KT::inv)
-          v[k] = (QMODE == QM_STEP_ZONAL) ? (int32_t)((uint32_t)qq * (uint32_t)qp.w[k] + (uint32_t)bias)
-                                          : (int32_t)(m * (uint32_t)qp.w[k] + (uint32_t)qp.kw[k]);
-      } else {
-        int32_t qq = z + zoff;  // the true coefficient
-        if (QMODE == QM_ZONAL) qq &= qp.keep[k];
-        q[j] = qq;
-        if (KT::inv) v[k] = (int32_t)((uint32_t)qq * (uint32_t)qp.w[k] + (uint32_t)bias);
-      }
-    }
-    if (KT::write_coef && QMODE != QM_ZONAL_ZZ) {
-      int4 u;
-      u.x = (int)pack16(q[0], q[1]);
-      u.y = (int)pack16(q[2], q[3]);
-      u.z = (int)pack16(q[4], q[5]);
-      u.w = (int)pack16(q[6], q[7]);
-      if (stage_coef) *(int4*)(stage_out + swz(lane, i)) = u;
-      else __stcs((int4*)coef_of(d, pos) + i, u);
-    }
-  }
-
-  // ---- inverse (8 column, then 8 row transposed butterflies) and output ----
-  uint32_t err = 0;
-  if (KT::inv) {
-    inv2d(v);
-    if (KT::sse) {
-      // squared error against the input rows, still in the input stage
-      const uint2* st = (const uint2*)in;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const uint2 x = st[i * 32 + lane];
-        const uint32_t e0 = __vabsdiffu4(pixels4(v[8 * i + 0], v[8 * i + 1], v[8 * i + 2], v[8 * i + 3]), x.x);
-        const uint32_t e1 = __vabsdiffu4(pixels4(v[8 * i + 4], v[8 * i + 5], v[8 * i + 6], v[8 * i + 7]), x.y);
-        err = __dp4a(e0, e0, err);
-        err = __dp4a(e1, e1, err);
-      }
-    } else {
-      const int64_t pitch = __ldg(&d->pitch);
-      uint8_t* o = dst_of(d) + (int64_t)(8 * pos.by) * pitch + 8 * pos.bx;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        uint2 w;
-        w.x = pixels4(v[8 * i + 0], v[8 * i + 1], v[8 * i + 2], v[8 * i + 3]);
-        w.y = pixels4(v[8 * i + 4], v[8 * i + 5], v[8 * i + 6], v[8 * i + 7]);
-        __stcs((uint2*)(o + i * pitch), w);
-      }
-    }
-  }
-  return err;
-}
-
-// Write a staged 32-block half-tile of coefficients back with 512-byte warp
-// stores.  The blocks of a plane are contiguous in coef, so when every active
-// lane is in lane 0's plane the half-tile is one contiguous range.
-__device__ __forceinline__ void write_back(const uint8_t* __restrict__ stage_out, const PlaneDesc* __restrict__ planes,
-                                          const Pos& pos, int lane) {
-  const bool active = pos.plane >= 0;
-  const int plane0 = __shfl_sync(0xffffffffu, pos.plane, 0);
-  const unsigned act = __ballot_sync(0xffffffffu, active);
-  int16_t* mine = active ? coef_of(planes + pos.plane, pos) : nullptr;
-  // Instruction k moves bytes [512 k, 512 k + 512) of the half-tile: lane l
-  // takes 16-byte chunk (l & 7) of block 4 k + (l >> 3), i.e. byte 512 k + 16 l;
-  // in shared memory that chunk sits at one of two lane-specific offsets (the
-  // swizzle depends on k only through k & 1) plus 512 k.
-  const int pb = lane >> 3, pc = lane & 7;
-  const uint32_t rd0 = pb * 128 + ((pc ^ pb) << 4), rd1 = pb * 128 + ((pc ^ (pb + 4)) << 4);
-  if (__all_sync(0xffffffffu, !active || pos.plane == plane0)) {
-    int4* gp = (int4*)__shfl_sync(0xffffffffu, (unsigned long long)mine, 0) + lane;
-    const int nact = __popc(act);  // active lanes are a prefix of the warp
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      if (4 * k + pb < nact) __stcs(gp + 32 * k, *(const int4*)(stage_out + 512 * k + ((k & 1) ? rd1 : rd0)));
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int b = 4 * k + pb;
-      int16_t* cb = (int16_t*)__shfl_sync(0xffffffffu, (unsigned long long)mine, b);
-      if (cb) __stcs((int4*)cb + pc, *(const int4*)(stage_out + 512 * k + ((k & 1) ? rd1 : rd0)));
-    }
-  }
-}
-
-// Write a staged 32-block half-tile of packed zonal coefficients (r int16 per
-// block, lane l's at [l r, l r + r)) back to memory.  When every active lane is
-// in lane 0's plane the half-tile is one contiguous range of 32 r values,
-// written as 4-byte words when aligned; otherwise each lane writes its own r.
-__device__ __forceinline__ void write_back_zz(const uint8_t* __restrict__ stage_out,
-                                             const PlaneDesc* __restrict__ planes, const Pos& pos, int lane, int r) {
-  const bool active = pos.plane >= 0;
-  const int plane0 = __shfl_sync(0xffffffffu, pos.plane, 0);
-  const unsigned act = __ballot_sync(0xffffffffu, active);
-  int16_t* mine = active ? coef_of_zz(planes + pos.plane, pos, r) : nullptr;
-  const int16_t* st16 = (const int16_t*)stage_out;
-  if (__all_sync(0xffffffffu, !active || pos.plane == plane0)) {
-    int16_t* base = (int16_t*)__shfl_sync(0xffffffffu, (unsigned long long)mine, 0);
-    const int n = __popc(act) * r;  // values to write
-    if (((uintptr_t)base & 3) == 0 && (n & 1) == 0) {
-      uint32_t* gw = (uint32_t*)base;
-      const uint32_t* sw = (const uint32_t*)st16;
-      for (int k = lane; k < n / 2; k += 32) __stcs(gw + k, sw[k]);
-    } else {
-      for (int k = lane; k < n; k += 32) base[k] = st16[k];
-    }
-  } else if (active) {
-    for (int t = 0; t < r; ++t) mine[t] = st16[lane * r + t];
-  }
-}
-
-template <int KIND, int QMODE, bool EVENQ>
-__global__ void __launch_bounds__(kMaxThreads, 3)
-k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts, int32_t nplanes, int64_t total,
-        int64_t chunk, int stage_coef, unsigned long long* __restrict__ sse, const QuantParams qp) {
-  using KT = KindTraits<KIND>;
-  using SP = SmemPlan<KIND>;
-  constexpr int kTile = 32 * kBpl;
-  extern __shared__ __align__(128) uint8_t smem[];
-  const int lane = threadIdx.x & 31;
-  uint8_t* wsm = smem + (threadIdx.x >> 5) * SP::warp;
-  uint8_t* stage_out = wsm + 2 * SP::in_stage;
-
-  const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t begin = gwarp * chunk;
-  if (begin >= total) return;  // whole warp exits together
-  const int64_t end = min(total, begin + chunk);
-  const int32_t rend = (int32_t)(end - begin);  // chunk length (< 2^31 blocks)
-
-  Cursor cur;
-  {
-    int lo = 0, hi = nplanes;  // largest p with starts[p] <= begin
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (__ldg(starts + mid) <= begin) lo = mid; else hi = mid;
-    }
-    cur.p = lo;
-    cur.first = (int32_t)(__ldg(starts + lo) - begin);
-    cur.next_start = (int32_t)min(__ldg(starts + lo + 1) - begin, (int64_t)0x7fffffff);
-    cur.last.plane = -1;
-    cur.last.by = cur.last.bx = 0;
-  }
-
-  // Issue the asynchronous input copies of one tile into stage s.
-  auto issue = [&](int s, const Pos* q) {
-#pragma unroll
-    for (int u = 0; u < kBpl; ++u) {
-      const uint32_t sa = smem_addr(wsm + s * SP::in_stage + u * SP::in_per32);
-      if (KT::in_pix) {
-        if (q[u].plane >= 0) {
-          const PlaneDesc* d = planes + q[u].plane;
-          const int64_t pitch = __ldg(&d->pitch);
-          const uint8_t* src = src_of(d) + (int64_t)(8 * q[u].by) * pitch + 8 * q[u].bx;
-#pragma unroll
-          for (int i = 0; i < 8; ++i) cp_async8(sa + (i * 32 + lane) * 8, src + i * pitch);
-        }
-      } else if (QMODE != QM_ZONAL_ZZ) {
-        // Coefficients: lane copies 16-byte chunk c of block b (512 contiguous
-        // bytes per warp instruction when the tile lies in one plane).
-        const int16_t* mine = q[u].plane >= 0 ? coef_of(planes + q[u].plane, q[u]) : nullptr;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int b = 4 * k + (lane >> 3), c = lane & 7;
-          const int16_t* cb = (const int16_t*)__shfl_sync(0xffffffffu, (unsigned long long)mine, b);
-          if (cb) cp_async16(sa + swz(b, c), cb + 8 * c);
-        }
-      }
-    }
-    cp_async_commit();
-  };
-
-  unsigned long long acc = 0;  // K_RT_SSE: this lane's error sum for plane acc_plane
-  int acc_plane = -1;
-  Pos pc[kBpl];
-#pragma unroll
-  for (int u = 0; u < kBpl; ++u) pc[u] = cur.locate(planes, starts, begin, 32 * u + lane, rend);
-  issue(0, pc);
-  int s = 0;
-  for (int32_t base = 0; base < rend; base += kTile, s ^= 1) {
-    const int32_t nbase = base + kTile;
-    __syncwarp();  // every lane is done reading stage s ^ 1 before it is refilled
-    Pos pn[kBpl];
-#pragma unroll
-    for (int u = 0; u < kBpl; ++u) pn[u] = cur.locate(planes, starts, begin, nbase + 32 * u + lane, rend);
-    if (nbase < rend) issue(s ^ 1, pn);
-    else cp_async_commit();
-    cp_async_wait<1>();
-    __syncwarp();
-
-#pragma unroll
-    for (int u = 0; u < kBpl; ++u) {
-      const uint32_t e = block_step<KIND, QMODE, EVENQ>(wsm + s * SP::in_stage + u * SP::in_per32,
-                                                        stage_out + u * kTileBytesOut, planes, pc[u], stage_coef, qp,
-                                                        lane);
-      if (KT::sse && pc[u].plane >= 0) {
-        if (pc[u].plane != acc_plane) {  // one atomic per lane per plane it visits
-          if (acc_plane >= 0) atomicAdd(sse + acc_plane, acc);
-          acc_plane = pc[u].plane;
-          acc = 0;
-        }
-        acc += e;
-      }
-    }
-
-    if (KT::write_coef && stage_coef) {
-      __syncwarp();
-#pragma unroll
-      for (int u = 0; u < kBpl; ++u) {
-        if (QMODE == QM_ZONAL_ZZ) write_back_zz(stage_out + u * kTileBytesOut, planes, pc[u], lane, qp.r);
-        else write_back(stage_out + u * kTileBytesOut, planes, pc[u], lane);
-      }
-      __syncwarp();
-    }
-#pragma unroll
-    for (int u = 0; u < kBpl; ++u) pc[u] = pn[u];
-  }
-  if (KT::sse && acc_plane >= 0) atomicAdd(sse + acc_plane, acc);
-  cp_async_wait<0>();
-}
-
-using KernelFn = void (*)(const PlaneDesc*, const int64_t*, int32_t, int64_t, int64_t, int, unsigned long long*,
-                          const QuantParams);
+constexpr int kZoneAll = 14;  // anti-diagonals 0..14: every coefficient
 
 template <int KIND, bool EVENQ>
 KernelFn pick_mode(int qmode) {
   switch (qmode) {
-    case QM_ZONAL_ZZ: return (KIND == K_RT_FULL || KIND == K_RT_COEF) ? k_codec<KIND, QM_ZONAL_ZZ, false>
-                                                                     : k_codec<KIND, QM_ZONAL, false>;
-    case QM_STEP: return k_codec<KIND, QM_STEP, EVENQ>;
-    case QM_ZONAL: return k_codec<KIND, QM_ZONAL, false>;
-    case QM_STEP_ZONAL: return k_codec<KIND, QM_STEP_ZONAL, EVENQ>;
-    default: return k_codec<KIND, QM_NONE, false>;
+    case QM_ZONAL_ZZ: return (KIND == K_RT_FULL || KIND == K_RT_COEF) ? k_codec<KIND, QM_ZONAL_ZZ, false, kZoneAll>
+                                                                     : k_codec<KIND, QM_ZONAL, false, kZoneAll>;
+    case QM_STEP: return k_codec<KIND, QM_STEP, EVENQ, kZoneAll>;
+    case QM_ZONAL: return k_codec<KIND, QM_ZONAL, false, kZoneAll>;
+    case QM_STEP_ZONAL: return k_codec<KIND, QM_STEP_ZONAL, EVENQ, kZoneAll>;
+    default: return k_codec<KIND, QM_NONE, false, kZoneAll>;
   }
 }
 
 template <bool EVENQ>
 KernelFn pick_kernel_q(int kind, int qmode) {
   switch (kind) {
-    case K_FORWARD: return k_codec<K_FORWARD, QM_NONE, false>;
+    case K_FORWARD: return k_codec<K_FORWARD, QM_NONE, false, kZoneAll>;
     case K_QUANTISE:
       switch (qmode) {
-        case QM_STEP: return k_codec<K_QUANTISE, QM_STEP, EVENQ>;
-        case QM_ZONAL: return k_codec<K_QUANTISE, QM_ZONAL, false>;
-        case QM_STEP_ZONAL: return k_codec<K_QUANTISE, QM_STEP_ZONAL, EVENQ>;
+        case QM_STEP: return k_codec<K_QUANTISE, QM_STEP, EVENQ, kZoneAll>;
+        case QM_ZONAL: return k_codec<K_QUANTISE, QM_ZONAL, false, kZoneAll>;
+        case QM_STEP_ZONAL: return k_codec<K_QUANTISE, QM_STEP_ZONAL, EVENQ, kZoneAll>;
         default: return nullptr;
       }
-    case K_INVERSE: return qmode == QM_ZONAL_ZZ ? k_codec<K_INVERSE, QM_ZONAL_ZZ, false> : k_codec<K_INVERSE, QM_NONE, false>;
+    case K_INVERSE:
+      return qmode == QM_ZONAL_ZZ ? k_codec<K_INVERSE, QM_ZONAL_ZZ, false, kZoneAll>
+                                  : k_codec<K_INVERSE, QM_NONE, false, kZoneAll>;
     case K_RT_FULL: return pick_mode<K_RT_FULL, EVENQ>(qmode);
     case K_RT_PIX: return pick_mode<K_RT_PIX, EVENQ>(qmode);
     case K_RT_COEF: return pick_mode<K_RT_COEF, EVENQ>(qmode);
@@ -534,20 +62,33 @@ int warp_smem(int kind) {
 }
 }  // namespace
 
+// CTAs per SM when the caller leaves the choice to the library (measured on
+// 256 x 1080x1920 batches): four, except three for the encode with dense
+// coefficient output, whose 192 bytes of traffic per block run best with
+// fewer requests in flight.  Capped at the resident count, which is three for
+// the kernels that use more than 128 registers.
+int default_ctas_per_sm(int kind, int qmode) { return (kind == K_RT_COEF && qmode != QM_ZONAL_ZZ) ? 3 : 4; }
+
 size_t codec_smem_bytes(const LaunchShape& shape, int kind) {
   return (size_t)(shape.threads / 32) * warp_smem(kind);
 }
 
 int codec_grid(const LaunchShape& shape, int sm_count, int64_t total) {
   int64_t want = (total + shape.threads - 1) / shape.threads;
-  const int64_t cap = (int64_t)sm_count * shape.ctas_per_sm;
+  const int64_t cap = (int64_t)sm_count * (shape.ctas_per_sm > 0 ? shape.ctas_per_sm : 4);
   if (want > cap) want = cap;
   return (int)(want < 1 ? 1 : want);
 }
 
 cudaError_t launch_codec(const CodecLaunch& c, const LaunchShape& shape, int sm_count, cudaStream_t stream) {
   if (c.total <= 0) return cudaSuccess;
-  KernelFn fn = pick_kernel(c.kind, c.qmode, c.evenq);
+  KernelFn fn = nullptr;
+  if (c.qmode == QM_ZONAL || c.qmode == QM_ZONAL_ZZ) {
+    const int zs = zone_for(c.qp.r);
+    if (zs <= kZoneLoMax) fn = pick_zonal_kernel_lo(c.kind, c.qmode, zs);
+    else if (zs <= kZoneHiMax) fn = pick_zonal_kernel_hi(c.kind, c.qmode, zs);
+  }
+  if (!fn) fn = pick_kernel(c.kind, c.qmode, c.evenq);
   if (!fn) return cudaErrorInvalidValue;
   if (shape.threads < 32 || shape.threads > kMaxThreads || shape.threads % 32) return cudaErrorInvalidValue;
   const size_t smem = codec_smem_bytes(shape, c.kind);
@@ -560,11 +101,12 @@ cudaError_t launch_codec(const CodecLaunch& c, const LaunchShape& shape, int sm_
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, fn, shape.threads, smem) != cudaSuccess || resident < 1)
     resident = 1;
   LaunchShape sh = shape;
+  if (sh.ctas_per_sm == 0) sh.ctas_per_sm = default_ctas_per_sm(c.kind, c.qmode);
   if (sh.ctas_per_sm > resident) sh.ctas_per_sm = resident;
   const int grid = codec_grid(sh, sm_count, c.total);
   const int64_t warps = (int64_t)grid * (shape.threads / 32);
   int64_t chunk = (c.total + warps - 1) / warps;
-  chunk = (chunk + 32 * kBpl - 1) / (32 * kBpl) * (32 * kBpl);
+  chunk = (chunk + kTile - 1) / kTile * kTile;
   fn<<<grid, shape.threads, smem, stream>>>(c.planes, c.starts, c.nplanes, c.total, chunk, shape.stage_coef, c.sse,
                                             c.qp);
   return cudaGetLastError();

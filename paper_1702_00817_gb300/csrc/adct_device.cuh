@@ -164,4 +164,20 @@ __host__ __device__ constexpr ZigZag make_zigzag() {
   return z;
 }
 
+// Zones of the zonal quantiser: zone s holds the coefficients on anti-diagonals
+// 0..s (i + j <= s); zone_count(s) of them.  The first r zig-zag positions lie
+// in zone zone_for(r); zones above kZoneHiMax are served by the full zone 14.
+__host__ __device__ constexpr int zone_count(int s) {
+  int n = 0;
+  for (int d = 0; d <= s; ++d) n += d < 8 ? d + 1 : 15 - d;
+  return n;
+}
+constexpr int kZoneLoMax = 4;  // zones 0..4: r <= 15
+constexpr int kZoneHiMax = 8;  // zones 5..8: r <= 43
+inline int zone_for(int r) {
+  for (int s = 0; s <= kZoneHiMax; ++s)
+    if (r <= zone_count(s)) return s;
+  return 14;
+}
+
 }  // namespace adct

@@ -1,5 +1,5 @@
 // Internal interface between the C-ABI layer (adct_api.cu) and the kernel
-// translation units (adct_codec.cu, adct_float.cu).  Not installed.
+// translation units (adct_codec*.cu, adct_float.cu, adct_quality.cu).  Not installed.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -37,6 +37,16 @@ struct CodecLaunch {
   unsigned long long* sse;  // K_RT_SSE: per-plane sums of squared reconstruction error (device)
   QuantParams qp;
 };
+
+// One instantiation of the integer codec kernel.
+using KernelFn = void (*)(const PlaneDesc*, const int64_t*, int32_t, int64_t, int64_t, int, unsigned long long*,
+                          const QuantParams);
+
+// Zonal kernels specialised on the zone (adct_codec_zonal_lo.cu: zones
+// 0..kZoneLoMax; adct_codec_zonal_hi.cu: up to kZoneHiMax); nullptr when the
+// kind / mode pair has no specialisation.
+KernelFn pick_zonal_kernel_lo(int kind, int qmode, int zs);
+KernelFn pick_zonal_kernel_hi(int kind, int qmode, int zs);
 
 // Launches the integer codec kernel.  Returns cudaSuccess or the launch error.
 cudaError_t launch_codec(const CodecLaunch& c, const LaunchShape& shape, int sm_count, cudaStream_t stream);

@@ -289,7 +289,17 @@ def test_autotune_keeps_results(codec):
     torch.cuda.synchronize()
     for x, d in zip(imgs, dsts):
         assert np.array_equal(d.cpu().numpy(), oracle.roundtrip(x, oracle.MODE_STEP, inputs.step_table(4))[1])
-    codec.set_launch(before["threads_per_cta"], before["ctas_per_sm"], before["stage_coef"])
+    codec.set_launch(before["threads_per_cta"], before["ctas_per_sm"] or -1, before["stage_coef"])
+
+
+def test_launch_shape_automatic_default():
+    c = Codec(0)
+    assert c.get_launch()["ctas_per_sm"] == 0  # chosen per kernel by the library
+    c.set_launch(64, 5, 0)
+    assert c.get_launch() == {"threads_per_cta": 64, "ctas_per_sm": 5, "stage_coef": 0, "reserved": 0}
+    c.set_launch(128, -1, 1)
+    assert c.get_launch()["ctas_per_sm"] == 0
+    c.close()
 
 
 def test_host_pipeline_equals_device_path(codec):

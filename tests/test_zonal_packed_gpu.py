@@ -57,7 +57,7 @@ def _check(codec, imgs, r, with_dst=True, stage_coef=1):
         codec.roundtrip([Image(s, d, c) for s, d, c in zip(srcs, dsts, coefs)], q)
         torch.cuda.synchronize()
     finally:
-        codec.set_launch(old["threads_per_cta"], old["ctas_per_sm"], old["stage_coef"])
+        codec.set_launch(old["threads_per_cta"], old["ctas_per_sm"] or -1, old["stage_coef"])
     for x, d, c in zip(imgs, dsts, coefs):
         cf = c.cpu().numpy().astype(np.int64)
         for k, plane in enumerate(_planes(x)):
@@ -215,3 +215,43 @@ def test_full_size_packed_sampled(codec):
         pref, rec_ref = _packed_ref(host[k], r)
         assert np.array_equal(dst[k].cpu().numpy(), rec_ref)
         assert np.array_equal(coef[k].cpu().numpy().astype(np.int64), pref)
+
+
+def test_every_r_every_zonal_kind(codec):
+    """r = 0..64 covers every zone the kernels are specialised on and both
+    sides of each zone boundary: dense and packed round trips, pixels only,
+    packed coefficients only, the packed inverse and the squared error."""
+    imgs = [inputs.synth_image(40, 264, 3)[0], inputs.synth_image(24, 16, 4, channels=3)]
+    srcs = [torch.from_numpy(np.ascontiguousarray(x)).to(DEV) for x in imgs]
+    for r in range(65):
+        refs = [[_packed_ref(p, r) for p in _planes(x)] for x in imgs]
+        dense_ref = [[oracle.roundtrip(p, oracle.MODE_ZONAL, None, r)[0] for p in _planes(x)] for x in imgs]
+        dz, pz = make_quant(ADCT_Q_ZONAL, None, r), make_quant(ADCT_Q_ZONAL_ZZ, None, r)
+        dense = [torch.empty((1 if x.ndim == 2 else x.shape[0], x.shape[-2] // 8, x.shape[-1] // 8, 8, 8),
+                             dtype=torch.int16, device=DEV) for x in imgs]
+        d1 = [torch.empty_like(s) for s in srcs]
+        codec.roundtrip([Image(s, d, c) for s, d, c in zip(srcs, d1, dense)], dz)
+        d2 = [torch.empty_like(s) for s in srcs]
+        codec.roundtrip([Image(s, d) for s, d in zip(srcs, d2)], pz)
+        d3 = [torch.empty_like(s) for s in srcs]
+        codec.roundtrip([Image(s, d) for s, d in zip(srcs, d3)], dz)
+        sse = codec.quality([Image(s) for s in srcs], dz).cpu().numpy()
+        if r > 0:
+            packed = [_packed_like(x, r) for x in imgs]
+            codec.roundtrip([Image(s, None, c) for s, c in zip(srcs, packed)], pz)
+            d4 = [torch.empty_like(s) for s in srcs]
+            codec.inverse([Image(None, d, c) for d, c in zip(d4, packed)], pz)
+        torch.cuda.synchronize()
+        plane = 0
+        for m, x in enumerate(imgs):
+            for k, p in enumerate(_planes(x)):
+                pref, rec_ref = refs[m][k]
+                pick = (lambda t: t.cpu().numpy()) if x.ndim == 2 else (lambda t, k=k: t[k].cpu().numpy())
+                assert np.array_equal(dense[m][k].cpu().numpy().astype(np.int64), dense_ref[m][k]), r
+                for out in (d1, d2, d3):
+                    assert np.array_equal(pick(out[m]), rec_ref), r
+                assert int(sse[plane]) == oracle.sse(rec_ref, p), r
+                if r > 0:
+                    assert np.array_equal(packed[m][k].cpu().numpy().astype(np.int64), pref), r
+                    assert np.array_equal(pick(d4[m]), rec_ref), r
+                plane += 1
