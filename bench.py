@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--images", type=int, default=N_IMG)
+    p.add_argument("--r", type=int, nargs="*", default=[1, 6, 10, 16, 25, 64],
+                   help="packed workload: zonal r values to sweep")
     return p.parse_args()
 
 
@@ -447,7 +449,7 @@ def run_packed(args):
     hsrc = torch.from_numpy(host).pin_memory() if not args.no_e2e else None
     hdst = torch.empty_like(hsrc).pin_memory() if not args.no_e2e else None
     rows = []
-    for r in (1, 6, 10, 16, 25, 64):
+    for r in args.r:
         packed = torch.empty((n, H // 8, W // 8, r), dtype=torch.int16, device=dev)
         row = {"r": r}
         for name, mode, coef, cpb in (("dense", ADCT_Q_ZONAL, dense, 64), ("packed", ADCT_Q_ZONAL_ZZ, packed, r)):
@@ -492,19 +494,21 @@ def run_packed(args):
             row["e2e_speedup"] = row["packed"]["e2e_blocks_s"] / row["dense"]["e2e_blocks_s"]
         rows.append(row)
         del packed
-    r10 = next(x for x in rows if x["r"] == 10)
+    r10 = next((x for x in rows if x["r"] == 10), rows[0])
+    rh = r10["r"]
     if d.rank == 0:
         line = {"metric": METRIC, "value": r10["packed"]["blocks_s"], "unit": "blocks/s", "n_gpus": d.ws,
                 "steps": steps, "warmup": max(3, args.warmup),
                 "ms_per_step": blocks / r10["packed"]["blocks_s"] * 1000.0, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
                 "config": {"workload": f"uniform batch {n}x{H}x{W} u8 zonal round trip, packed r int16 per block "
-                                       f"(zig-zag) vs dense 64; headline value r = 10 packed",
+                                       f"(zig-zag) vs dense 64; headline value r = {rh} packed",
                            "l2": "inputs larger than L2"},
                 "roofline": {"bound": "hbm", "achieved": r10["packed"]["gbs"], "peak": peak, "unit": "GB/s",
                              "frac": r10["packed"]["frac"], "peak_kind": peak_kind,
-                             "kernel": "k_codec<RT_FULL, ZONAL_ZZ>", "traffic": None,
-                             "algorithmic_bytes_per_launch": blocks * (128 + 20)},
+                             "kernel": "k_codec<RT_FULL, ZONAL_ZZ>",
+                             "traffic": recorded_traffic(f"k_codec_rt_zz{rh}"),
+                             "algorithmic_bytes_per_launch": blocks * (128 + 2 * rh)},
                 "sweep": rows}
         print(json.dumps(line), flush=True)
     codec.close()
@@ -531,16 +535,21 @@ def run_ragged(args):
     import torch
 
     from paper_1702_00817_gb300 import _build, inputs
-    from paper_1702_00817_gb300.codec import ADCT_Q_STEP, Codec, Image, image_array, make_quant
+    from paper_1702_00817_gb300.codec import ADCT_Q_STEP, Codec, Image, image_array, make_quant, shard_plan
     d = Dist()
     dev = torch.device("cuda", d.local)
     torch.cuda.set_device(dev)
     if d.rank == 0 or not _build.up_to_date():
         _build.build()
     d.barrier()
-    n = 1000
-    sizes = inputs.ragged_sizes(n, seed=inputs.BASE_SEED + d.rank)
-    srcs = [inputs.synth_image_device(h, w, inputs.BASE_SEED + d.rank * n + k, 3, dev) for k, (h, w) in enumerate(sizes)]
+    # one ragged batch of 1000 images per GPU, sharded over the ranks by the
+    # library's balanced plan (each rank computes it alone: no exchange)
+    n_global = 1000 * d.ws
+    sizes_all = inputs.ragged_sizes(n_global, seed=inputs.BASE_SEED)
+    mine, max_blocks = shard_plan([(3, h, w) for h, w in sizes_all], d.ws, d.rank)
+    n = len(mine)
+    sizes = [sizes_all[i] for i in mine]
+    srcs = [inputs.synth_image_device(h, w, inputs.BASE_SEED + i, 3, dev) for i, (h, w) in zip(mine, sizes)]
     dsts = [torch.empty_like(x) for x in srcs]
     coefs = [torch.empty((3, h // 8, w // 8, 8, 8), dtype=torch.int16, device=dev) for (h, w) in sizes]
     images = [Image(s_, d_, c_) for s_, d_, c_ in zip(srcs, dsts, coefs)]
@@ -589,8 +598,10 @@ def run_ragged(args):
         line = {"metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": d.ws, "steps": steps,
                 "warmup": max(3, args.warmup), "ms_per_step": 1000 * t_graph / steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-                "config": {"workload": f"ragged batch {n} x 3-channel u8, sides 8*round(2^U[6,12]/8), step s=4, "
-                                       f"one graph-captured launch per step", "blocks_per_gpu": blocks,
+                "config": {"workload": f"ragged batch {n_global} x 3-channel u8, sides 8*round(2^U[6,12]/8), "
+                                       f"step s=4, one graph-captured launch per step per GPU",
+                           "blocks_per_gpu": blocks, "max_blocks_per_gpu": max_blocks,
+                           "parallelism": f"dp{d.ws} (images sharded by adct_shard_plan, no collective)",
                            "l2": "inputs larger than L2", "autotuned_launch": best, "autotune_us": best_us},
                 "forms": {"graph_one_launch_blocks_s": value, "eager_one_launch_blocks_s": total / t_eager,
                           "per_image_loop_blocks_s": total / t_loop, "graph_vs_loop": t_loop / t_graph,

@@ -253,6 +253,23 @@ adct_status adct_roundtrip_host(adct_context* ctx, const adct_image* host_imgs, 
                                 int64_t chunk_bytes);
 
 /*
+ * Multi-GPU sharding of one batch, with no collective (the blocks of different
+ * images never interact, Sec. 3): a deterministic partition of the n images
+ * over `world` ranks balanced by 8x8 block count -- images taken largest first
+ * (ties: lower index), each given to the rank with the fewest blocks so far
+ * (ties: lower rank).  Every rank computes the same plan on its own.  Only the
+ * shape fields of imgs are read (pointers may be NULL); shapes are validated
+ * as for adct_roundtrip.  Writes the indices of the images of `rank`, in
+ * increasing order, to out (host array with room for n) and their number to
+ * *count; *max_blocks (nullable) receives the largest per-rank block total.
+ * Host only: no device or context is used.  Errors: ADCT_ERR_INVALID_ARG for
+ * world < 1, rank outside [0, world) or NULL out/count; ADCT_ERR_SHAPE for a
+ * bad image shape.
+ */
+adct_status adct_shard_plan(const adct_image* imgs, int32_t n, int32_t world, int32_t rank, int32_t* out,
+                            int32_t* count, int64_t* max_blocks);
+
+/*
  * Diagnostic (host-side, no GPU needed): run the library's own 8-point
  * butterfly -- the same template the kernels instantiate -- on `count`
  * vectors of 8 int32 in place, forward (X = T x) or inverse (x = T^T X), and

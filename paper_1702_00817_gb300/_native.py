@@ -30,7 +30,7 @@ EXPORTS = (
     "adct_forward_f32", "adct_backward_f32", "adct_set_launch", "adct_get_launch", "adct_roundtrip_graph",
     "adct_autotune", "adct_roundtrip_host", "adct_butterfly_host", "adct_kernel_timing", "adct_kernel_time",
     "adct_roundtrip_noalloc", "adct_quality", "adct_quality_dct", "adct_server_create", "adct_server_destroy", "adct_server_encode",
-    "adct_server_decode", "adct_server_poll", "adct_server_stats", "adct_server_clock",
+    "adct_server_decode", "adct_server_poll", "adct_server_stats", "adct_server_clock", "adct_shard_plan",
     "adct_status_string", "adct_last_error",
 )
 
@@ -133,6 +133,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "adct_server_poll": ([P, ctypes.POINTER(adct_completion), i32, i32], i32),
         "adct_server_stats": ([P, ctypes.POINTER(adct_server_stats_t)], i32),
         "adct_server_clock": ([], ctypes.c_double),
+        "adct_shard_plan": ([I, i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i64)], i32),
         "adct_status_string": ([i32], ctypes.c_char_p),
         "adct_last_error": ([P], ctypes.c_char_p),
     }

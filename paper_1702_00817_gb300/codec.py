@@ -260,6 +260,25 @@ class Codec:
         return gx
 
 
+def shard_plan(shapes, world: int, rank: int):
+    """Indices of the images of `rank` in the balanced no-collective partition
+    of a batch over `world` GPUs (adct_shard_plan), and the largest per-rank
+    block total.  shapes: (height, width) or (channels, height, width) tuples."""
+    n = len(shapes)
+    arr = (N.adct_image * max(1, n))()
+    for k, sh in enumerate(shapes):
+        c, h, w = (1, *sh) if len(sh) == 2 else sh
+        arr[k].width, arr[k].height, arr[k].channels = int(w), int(h), int(c)
+        arr[k].pitch, arr[k].plane_stride = int(w), int(w) * int(h)
+    out = (ctypes.c_int32 * max(1, n))()
+    count = ctypes.c_int32(0)
+    mx = ctypes.c_int64(0)
+    lib = N.load()
+    N.check(lib.adct_shard_plan(arr, n, int(world), int(rank), out, ctypes.byref(count), ctypes.byref(mx)), None,
+            "adct_shard_plan")
+    return [out[k] for k in range(count.value)], mx.value
+
+
 def butterfly_host(vectors, inverse: bool = False):
     """Run the library's 8-point butterfly on the host; returns (outputs, adds per transform)."""
     import numpy as np

@@ -934,6 +934,47 @@ adct_status adct_roundtrip_host(adct_context* ctx, const adct_image* himgs, int3
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// Sharding plan for several GPUs (host only).
+extern "C" adct_status adct_shard_plan(const adct_image* imgs, int32_t n, int32_t world, int32_t rank, int32_t* out,
+                                       int32_t* count, int64_t* max_blocks) {
+  if (world < 1 || rank < 0 || rank >= world || n < 0 || (n > 0 && !imgs) || !out || !count)
+    return ADCT_ERR_INVALID_ARG;
+  std::vector<int64_t> blocks((size_t)n);
+  for (int32_t m = 0; m < n; ++m) {
+    const adct_image& im = imgs[m];
+    if (im.width <= 0 || im.height <= 0 || im.width % 8 || im.height % 8 || im.width > 65536 || im.height > 65536 ||
+        im.channels < 1)
+      return ADCT_ERR_SHAPE;
+    blocks[m] = (int64_t)(im.width / 8) * (im.height / 8) * im.channels;
+  }
+  std::vector<int32_t> order((size_t)n);
+  for (int32_t m = 0; m < n; ++m) order[m] = m;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return blocks[a] > blocks[b]; });
+  // min-heap of (load, rank): the least-loaded rank, lowest rank first on ties
+  std::vector<std::pair<int64_t, int32_t>> heap;
+  for (int32_t r = 0; r < world; ++r) heap.emplace_back(0, r);
+  auto greater = [](const std::pair<int64_t, int32_t>& a, const std::pair<int64_t, int32_t>& b) { return a > b; };
+  std::make_heap(heap.begin(), heap.end(), greater);
+  std::vector<int32_t> owner((size_t)n);
+  for (int32_t m : order) {
+    std::pop_heap(heap.begin(), heap.end(), greater);
+    owner[m] = heap.back().second;
+    heap.back().first += blocks[m];
+    std::push_heap(heap.begin(), heap.end(), greater);
+  }
+  int32_t k = 0;
+  for (int32_t m = 0; m < n; ++m)
+    if (owner[m] == rank) out[k++] = m;
+  *count = k;
+  if (max_blocks) {
+    int64_t mx = 0;
+    for (const auto& h : heap) mx = std::max(mx, h.first);
+    *max_blocks = mx;
+  }
+  return ADCT_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Host-side diagnostic: the kernels' own butterfly templates on a counting type.
 namespace {
 thread_local int64_t g_adds = 0;

@@ -85,3 +85,29 @@ def test_make_quant_validates():
         make_quant(1, np.arange(1, 10))
     with pytest.raises(ValueError):
         make_quant(1, np.full(64, 70000))
+
+
+def test_shard_plan_is_a_balanced_partition():
+    from paper_1702_00817_gb300 import _native, inputs
+    from paper_1702_00817_gb300.codec import AdctError, shard_plan
+    sizes = inputs.ragged_sizes(1000, seed=3)
+    blocks = [(h // 8) * (w // 8) for h, w in sizes]
+    for world in (1, 2, 3, 8):
+        plans = [shard_plan(sizes, world, r) for r in range(world)]
+        idx = sorted(i for p, _ in plans for i in p)
+        assert idx == list(range(len(sizes)))                     # every image exactly once
+        loads = [sum(blocks[i] for i in p) for p, _ in plans]
+        assert all(mx == max(loads) for _, mx in plans)
+        assert max(loads) <= sum(blocks) / world + max(blocks)    # list-scheduling bound
+        assert all(p == sorted(p) for p, _ in plans)
+    assert shard_plan(sizes, 1, 0)[0] == list(range(len(sizes)))
+    # ties: equal images alternate over the ranks in index order
+    assert shard_plan([(8, 8)] * 4, 2, 0)[0] == [0, 2]
+    assert shard_plan([], 4, 3) == ([], 0)
+    for bad in ((2, 2), (2, -1), (0, 0)):
+        with pytest.raises(AdctError) as e:
+            shard_plan(sizes, *bad)
+        assert e.value.status == _native.ADCT_ERR_INVALID_ARG
+    with pytest.raises(AdctError) as e:
+        shard_plan([(12, 8)], 2, 0)
+    assert e.value.status == _native.ADCT_ERR_SHAPE
