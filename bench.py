@@ -198,7 +198,8 @@ def measured_peaks():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("adct_codec_kernel.cuh", "adct_codec.cu", "adct_device.cuh"):
+    for f in ("adct_codec_kernel.cuh", "adct_codec.cu", "adct_device.cuh", "adct_codec_zonal_lo.cu",
+              "adct_codec_zonal_hi.cu"):
         with open(os.path.join(ROOT, "paper_1702_00817_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -49,7 +49,7 @@ typedef struct CUstream_st* adct_stream_t;
 typedef enum {
   ADCT_OK = 0,
   ADCT_ERR_INVALID_ARG = 1, /* null pointer, bad count, bad quantiser or launch parameter */
-  ADCT_ERR_SHAPE = 2,       /* width/height not a positive multiple of 8, bad pitch/stride */
+  ADCT_ERR_SHAPE = 2,       /* width/height outside 1..65536 (multiples of 8 where required), bad pitch/stride */
   ADCT_ERR_ALIGN = 3,       /* src/dst/pitch/plane_stride not 8-byte, coef not 16-byte aligned */
   ADCT_ERR_OOM = 4,         /* workspace allocation failed */
   ADCT_ERR_CUDA = 5,        /* a CUDA call failed; see adct_last_error */
@@ -63,15 +63,28 @@ enum { ADCT_Q_NONE = 0, ADCT_Q_STEP = 1, ADCT_Q_ZONAL = 2, ADCT_Q_STEP_ZONAL = 3
 
 typedef struct adct_context adct_context;
 
+/* Pixel layouts (adct_image.layout). */
+enum { ADCT_LAYOUT_PLANAR = 0, ADCT_LAYOUT_INTERLEAVED = 1 };
+
 /*
- * One image of `channels` planar uint8 planes, each height x width (multiples of
- * 8, 8..65536), rows `pitch` bytes apart (pitch >= width), planes
- * `plane_stride` bytes apart (plane_stride >= pitch * height when channels > 1).
- * src and dst share pitch and plane_stride.
+ * One uint8 image of `channels` channels, height x width pixels (each side
+ * 1..65536).  Sides that are not multiples of 8 are covered by ceil(side / 8)
+ * blocks whose missing pixels replicate the last column / row of the image
+ * (JPEG-style edge extension); reconstructions write only the image's pixels.
+ *   layout ADCT_LAYOUT_PLANAR: `channels` planes, rows `pitch` bytes apart
+ *          (pitch >= width), planes `plane_stride` bytes apart
+ *          (plane_stride >= pitch * height when channels > 1).
+ *   layout ADCT_LAYOUT_INTERLEAVED: channels = 3 or 4 interleaved per pixel
+ *          (HWC: pixel (y, x), channel c at y * pitch + x * channels + c), rows
+ *          `pitch` bytes apart (pitch >= width * channels); plane_stride unused.
+ * src and dst share the layout, pitch and plane_stride; pitch and plane_stride
+ * are multiples of 8.
  *   src   pixels read by the forward transform            (8-byte aligned)
  *   dst   reconstructed pixels (may equal src)            (8-byte aligned)
- *   coef  int16 coefficients, block-major:  coef[((c * Hb + by) * Wb + bx) * 64 + i * 8 + j]
- *         with Hb = height/8, Wb = width/8, (i, j) = (row, column) frequency  (16-byte aligned)
+ *   coef  int16 coefficients, planar and block-major for both pixel layouts:
+ *         coef[((c * Hb + by) * Wb + bx) * 64 + i * 8 + j]
+ *         with Hb = ceil(height / 8), Wb = ceil(width / 8), (i, j) = (row, column)
+ *         frequency  (16-byte aligned).
  *         With the quantiser mode ADCT_Q_ZONAL_ZZ coef is packed instead: r int16
  *         per block, coef[((c * Hb + by) * Wb + bx) * r + t] = the coefficient at
  *         zig-zag position t (t < r); only 2-byte alignment of the plane blocks
@@ -86,7 +99,7 @@ typedef struct {
   int32_t width;
   int32_t height;
   int32_t channels;
-  int32_t reserved; /* must be 0 */
+  int32_t layout; /* ADCT_LAYOUT_* */
   int64_t pitch;
   int64_t plane_stride;
 } adct_image;

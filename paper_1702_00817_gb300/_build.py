@@ -11,8 +11,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libadct.so")
-SOURCES = ["adct_api.cu", "adct_codec.cu", "adct_codec_zonal_lo.cu", "adct_codec_zonal_hi.cu", "adct_float.cu",
-           "adct_quality.cu", "adct_server.cu"]
+SOURCES = ["adct_api.cu", "adct_codec.cu", "adct_codec_zonal_lo.cu", "adct_codec_zonal_hi.cu",
+           "adct_codec_interleaved.cu", "adct_codec_edge.cu", "adct_float.cu", "adct_quality.cu", "adct_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

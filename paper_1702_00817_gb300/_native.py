@@ -23,6 +23,7 @@ ADCT_ERR_TOO_LARGE = 8
 NOALLOC_MAX_PLANES = 1024
 
 ADCT_Q_NONE, ADCT_Q_STEP, ADCT_Q_ZONAL, ADCT_Q_STEP_ZONAL, ADCT_Q_ZONAL_ZZ = 0, 1, 2, 3, 4
+ADCT_LAYOUT_PLANAR, ADCT_LAYOUT_INTERLEAVED = 0, 1
 
 # Every symbol include/adct.h declares.
 EXPORTS = (
@@ -43,7 +44,7 @@ class adct_image(ctypes.Structure):
         ("width", ctypes.c_int32),
         ("height", ctypes.c_int32),
         ("channels", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("layout", ctypes.c_int32),
         ("pitch", ctypes.c_int64),
         ("plane_stride", ctypes.c_int64),
     ]

@@ -5,9 +5,10 @@ torch tensors into adct_image / adct_quant structures, passes the current
 CUDA stream, and raises AdctError on a non-OK status.
 
 Tensor conventions (matching include/adct.h):
-  pixels  uint8 [C, H, W] or [H, W], unit stride along W (rows and planes may be pitched)
-  coef    int16 with C * H * W elements, contiguous; block-major [C, H/8, W/8, 8, 8]
-          (ADCT_Q_ZONAL_ZZ: packed, C * H/8 * W/8 * r elements, [C, H/8, W/8, r], zig-zag order)
+  pixels  uint8 [C, H, W] or [H, W], unit stride along W (rows and planes may be pitched);
+          with Image(..., interleaved=True) uint8 [H, W, C], C = 3 or 4, channels adjacent
+  coef    int16, contiguous, block-major [C, Hb, Wb, 8, 8] with Hb = ceil(H/8), Wb = ceil(W/8)
+          (ADCT_Q_ZONAL_ZZ: packed [C, Hb, Wb, r], zig-zag order)
   float   float32 [..., H, W] contiguous
 """
 from __future__ import annotations
@@ -44,25 +45,35 @@ def coef_per_block(quant) -> int:
 
 @dataclass
 class Image:
-    """One image for the codec: any of src/dst (uint8 pixels) and coef (int16)."""
+    """One image for the codec: any of src/dst (uint8 pixels) and coef (int16);
+    interleaved: the pixel tensors are [H, W, C] (HWC, C = 3 or 4)."""
     src: torch.Tensor | None = None
     dst: torch.Tensor | None = None
     coef: torch.Tensor | None = None
+    interleaved: bool = False
 
 
-def _pix_geometry(t: torch.Tensor):
+def _pix_geometry(t: torch.Tensor, interleaved: bool = False):
     if t.dtype != torch.uint8:
         raise TypeError("pixel tensors must be uint8")
+    if interleaved:
+        if t.dim() != 3 or t.stride(2) != 1 or t.stride(1) != t.shape[2]:
+            raise ValueError("interleaved pixel tensors are [H, W, C] with adjacent channels")
+        H, W, C = t.shape
+        # a single row's pitch is never used (torch may report any stride for it)
+        return C, H, W, t.stride(0) if H > 1 else (W * C + 7) // 8 * 8, 0
     if t.dim() == 2:
         H, W = t.shape
-        if t.stride(1) != 1:
+        if t.stride(1) != 1 and W > 1:
             raise ValueError("pixel rows need unit stride")
-        return 1, H, W, t.stride(0), t.stride(0) * H
+        pitch = t.stride(0) if H > 1 else (W + 7) // 8 * 8
+        return 1, H, W, pitch, pitch * H
     if t.dim() == 3:
         C, H, W = t.shape
-        if t.stride(2) != 1:
+        if t.stride(2) != 1 and W > 1:
             raise ValueError("pixel rows need unit stride")
-        return C, H, W, t.stride(1), t.stride(0)
+        pitch = t.stride(1) if H > 1 else (W + 7) // 8 * 8
+        return C, H, W, pitch, t.stride(0) if C > 1 else pitch * H
     raise ValueError("pixel tensors are [H, W] or [C, H, W]")
 
 
@@ -72,28 +83,29 @@ def image_struct(im, cpb: int = 64) -> N.adct_image:
     ref = im.src if im.src is not None else im.dst
     s = N.adct_image()
     if ref is not None:
-        C, H, W, pitch, pstride = _pix_geometry(ref)
+        C, H, W, pitch, pstride = _pix_geometry(ref, im.interleaved)
         if im.src is not None and im.dst is not None:
-            g2 = _pix_geometry(im.dst)
+            g2 = _pix_geometry(im.dst, im.interleaved)
             if g2 != (C, H, W, pitch, pstride):
                 raise ValueError("src and dst must share shape, pitch and plane stride")
     elif im.coef is not None:
-        # coefficient-only image: [C, H/8, W/8, 8, 8], or [C, H/8, W/8, r] packed
+        # coefficient-only image: [C, Hb, Wb, 8, 8], or [C, Hb, Wb, r] packed
         if im.coef.dim() != (5 if cpb == 64 else 4):
-            raise ValueError("a coefficient-only image needs coef shaped [C, H/8, W/8, 8, 8] "
-                             "([C, H/8, W/8, r] for the packed zonal layout)")
+            raise ValueError("a coefficient-only image needs coef shaped [C, Hb, Wb, 8, 8] "
+                             "([C, Hb, Wb, r] for the packed zonal layout)")
         C, hb, wb = im.coef.shape[:3]
         H, W, pitch, pstride = hb * 8, wb * 8, wb * 8, hb * 8 * wb * 8
     else:
         raise ValueError("image has no tensors")
     if im.coef is not None:
-        if (im.coef.dtype != torch.int16 or not im.coef.is_contiguous()
-                or im.coef.numel() != C * (H // 8) * (W // 8) * cpb):
+        nb = ((H + 7) // 8) * ((W + 7) // 8)
+        if im.coef.dtype != torch.int16 or not im.coef.is_contiguous() or im.coef.numel() != C * nb * cpb:
             raise ValueError(f"coef must be contiguous int16 with {cpb} elements per 8x8 block")
     s.src = im.src.data_ptr() if im.src is not None else None
     s.dst = im.dst.data_ptr() if im.dst is not None else None
     s.coef = im.coef.data_ptr() if im.coef is not None else None
-    s.width, s.height, s.channels, s.reserved = W, H, C, 0
+    s.width, s.height, s.channels = W, H, C
+    s.layout = N.ADCT_LAYOUT_INTERLEAVED if im.interleaved and ref is not None else N.ADCT_LAYOUT_PLANAR
     s.pitch, s.plane_stride = pitch, pstride
     return s
 

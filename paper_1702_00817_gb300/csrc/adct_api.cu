@@ -194,55 +194,149 @@ adct_status build_quant(adct_context* ctx, const adct_quant* q, bool pixel_input
 
 enum Need { NEED_SRC = 1, NEED_DST = 2, NEED_COEF = 4 };
 
-// Validates the images and builds the plane descriptor table; cpb is the
-// number of int16 coefficients stored per block (64, or r when packed).
-adct_status build_planes(adct_context* ctx, const adct_image* imgs, int32_t n, int need, std::vector<PlaneDesc>& planes,
-                         std::vector<int64_t>& starts, int32_t cpb = 64) {
-  if (n < 0) return fail(ctx, ADCT_ERR_INVALID_ARG, "negative image count");
-  if (n > 0 && !imgs) return fail(ctx, ADCT_ERR_INVALID_ARG, "imgs is NULL");
-  planes.clear();
-  starts.clear();
-  int64_t total = 0;
-  for (int32_t m = 0; m < n; ++m) {
-    const adct_image& im = imgs[m];
-    const std::string at = " (image " + std::to_string(m) + ")";
-    if (im.width <= 0 || im.height <= 0 || im.width % 8 || im.height % 8 || im.width > 65536 || im.height > 65536)
-      return fail(ctx, ADCT_ERR_SHAPE, "width/height must be positive multiples of 8 up to 65536" + at);
-    if (im.channels < 1 || im.reserved != 0) return fail(ctx, ADCT_ERR_INVALID_ARG, "bad channels/reserved" + at);
-    if (im.pitch < im.width) return fail(ctx, ADCT_ERR_SHAPE, "pitch < width" + at);
-    if (im.channels > 1 && im.plane_stride < im.pitch * im.height)
-      return fail(ctx, ADCT_ERR_SHAPE, "plane_stride < pitch * height" + at);
-    if ((need & NEED_SRC) && !im.src) return fail(ctx, ADCT_ERR_INVALID_ARG, "src is NULL" + at);
-    if ((need & NEED_DST) && !im.dst) return fail(ctx, ADCT_ERR_INVALID_ARG, "dst is NULL" + at);
-    if ((need & NEED_COEF) && !im.coef) return fail(ctx, ADCT_ERR_INVALID_ARG, "coef is NULL" + at);
+// Checks one image; on error returns the status and sets *why.  coef_only:
+// the call reads and writes coefficients only, so the pixel layout is
+// irrelevant.
+adct_status check_image(const adct_image& im, int need, bool coef_only, const char** why) {
+  if (im.width <= 0 || im.height <= 0 || im.width > 65536 || im.height > 65536)
+    return *why = "width/height must be in 1..65536", ADCT_ERR_SHAPE;
+  if (im.layout != ADCT_LAYOUT_PLANAR && im.layout != ADCT_LAYOUT_INTERLEAVED)
+    return *why = "unknown layout", ADCT_ERR_INVALID_ARG;
+  if (im.channels < 1) return *why = "channels must be at least 1", ADCT_ERR_INVALID_ARG;
+  const bool inter = im.layout == ADCT_LAYOUT_INTERLEAVED && !coef_only;
+  if (inter && im.channels != 3 && im.channels != 4)
+    return *why = "interleaved images have 3 or 4 channels", ADCT_ERR_UNSUPPORTED;
+  if ((need & NEED_SRC) && !im.src) return *why = "src is NULL", ADCT_ERR_INVALID_ARG;
+  if ((need & NEED_DST) && !im.dst) return *why = "dst is NULL", ADCT_ERR_INVALID_ARG;
+  if ((need & NEED_COEF) && !im.coef) return *why = "coef is NULL", ADCT_ERR_INVALID_ARG;
+  if ((uintptr_t)im.coef % 16) return *why = "coef needs 16-byte alignment", ADCT_ERR_ALIGN;
+  if (need & (NEED_SRC | NEED_DST)) {
+    if (im.pitch < (int64_t)im.width * (inter ? im.channels : 1)) return *why = "pitch too small", ADCT_ERR_SHAPE;
+    if (!inter && im.channels > 1 && im.plane_stride < im.pitch * im.height)
+      return *why = "plane_stride < pitch * height", ADCT_ERR_SHAPE;
     if ((uintptr_t)im.src % 8 || (uintptr_t)im.dst % 8 || im.pitch % 8 ||
-        (im.channels > 1 && im.plane_stride % 8) || (uintptr_t)im.coef % 16)
-      return fail(ctx, ADCT_ERR_ALIGN, "src/dst/pitch/plane_stride need 8-byte, coef 16-byte alignment" + at);
-    const int32_t wb = im.width / 8, hb = im.height / 8;
-    const int64_t nb = (int64_t)wb * hb;
-    for (int32_t c = 0; c < im.channels; ++c) {
-      PlaneDesc d;
-      d.src = im.src ? im.src + (int64_t)c * im.plane_stride : nullptr;
-      d.dst = im.dst ? im.dst + (int64_t)c * im.plane_stride : nullptr;
-      d.coef = im.coef ? im.coef + (int64_t)c * nb * cpb : nullptr;
-      d.pitch = im.pitch;
-      d.first = total;
-      d.wb = wb;
-      d.hb = hb;
-      planes.push_back(d);
-      starts.push_back(total);
-      total += nb;
-    }
+        (!inter && im.channels > 1 && im.plane_stride % 8))
+      return *why = "src/dst/pitch/plane_stride need 8-byte alignment", ADCT_ERR_ALIGN;
   }
-  starts.push_back(total);
   return ADCT_OK;
 }
 
-size_t table_bytes(size_t nplanes) { return nplanes * sizeof(PlaneDesc) + (nplanes + 1) * sizeof(int64_t); }
+// Appends image im's descriptors (one per planar plane, or one for an
+// interleaved image) to out[*count..]; cpb is the number of int16
+// coefficients stored per block (64, or r when packed); plane_id numbers
+// channel 0 of the image among all planes of the call.  Returns the group:
+// 0 planar, 1 planar with edge blocks, 2 interleaved 3 channels, 3
+// interleaved 4 channels.
+int group_of(const adct_image& im, bool coef_only) {
+  if (coef_only) return 0;
+  if (im.layout == ADCT_LAYOUT_INTERLEAVED) return im.channels == 3 ? 2 : 3;
+  return (im.width % 8 || im.height % 8) ? 1 : 0;
+}
 
-void fill_table(void* host, const std::vector<PlaneDesc>& planes, const std::vector<int64_t>& starts) {
-  std::memcpy(host, planes.data(), planes.size() * sizeof(PlaneDesc));
-  std::memcpy((char*)host + planes.size() * sizeof(PlaneDesc), starts.data(), starts.size() * sizeof(int64_t));
+int describe_image(const adct_image& im, int32_t cpb, bool coef_only, int32_t plane_id, PlaneDesc* out,
+                   int32_t* count) {
+  const int32_t wb = (im.width + 7) / 8, hb = (im.height + 7) / 8;
+  const int64_t nb = (int64_t)wb * hb;
+  const bool inter = group_of(im, coef_only) >= 2;
+  PlaneDesc d{};
+  d.pitch = im.pitch;
+  d.cstride = nb * cpb;
+  d.wb = wb;
+  d.hb = hb;
+  d.ew = im.width - 8 * (wb - 1);
+  d.eh = im.height - 8 * (hb - 1);
+  if (inter) {
+    d.src = im.src;
+    d.dst = im.dst;
+    d.coef = im.coef;
+    d.plane_id = plane_id;
+    d.nch = im.channels;
+    out[(*count)++] = d;
+    return im.channels == 3 ? 2 : 3;
+  }
+  for (int32_t c = 0; c < im.channels; ++c) {
+    d.src = im.src ? im.src + (int64_t)c * im.plane_stride : nullptr;
+    d.dst = im.dst ? im.dst + (int64_t)c * im.plane_stride : nullptr;
+    d.coef = im.coef ? im.coef + (int64_t)c * nb * cpb : nullptr;
+    d.plane_id = plane_id + c;
+    d.nch = 1;
+    out[(*count)++] = d;
+  }
+  return (!coef_only && (im.width % 8 || im.height % 8)) ? 1 : 0;
+}
+
+// Work units of one call: one group (one launch) per pixel layout class;
+// planar images with edge blocks get their own launch so that the others run
+// kernels with the edge handling compiled out.
+constexpr int kGroups = 4;
+constexpr int kGroupNch[kGroups] = {1, 1, 3, 4};
+constexpr bool kGroupEdge[kGroups] = {false, true, true, true};
+
+int64_t blocks_of(const adct_image& im) { return (int64_t)((im.width + 7) / 8) * ((im.height + 7) / 8); }
+
+struct Tables {
+  std::vector<PlaneDesc> planes[kGroups];
+  std::vector<int64_t> starts[kGroups];  // flat-index prefix per group (nplanes + 1)
+  int32_t nplanes = 0;                   // planes of the call (per-plane outputs)
+  int64_t blocks = 0;                    // 8x8 blocks of the call, all channels
+  std::vector<uint8_t> blob;             // the groups' tables back to back, as uploaded
+  size_t off_planes[kGroups], off_starts[kGroups];
+
+  int64_t total(int g) const { return starts[g].empty() ? 0 : starts[g].back(); }
+  void serialise() {
+    size_t off = 0;
+    for (int g = 0; g < kGroups; ++g) {
+      off_planes[g] = off;
+      off += planes[g].size() * sizeof(PlaneDesc);
+      off_starts[g] = off;
+      off += starts[g].size() * sizeof(int64_t);
+    }
+    blob.resize(off);
+    for (int g = 0; g < kGroups; ++g) {
+      if (!planes[g].empty()) std::memcpy(blob.data() + off_planes[g], planes[g].data(), planes[g].size() * sizeof(PlaneDesc));
+      if (!starts[g].empty()) std::memcpy(blob.data() + off_starts[g], starts[g].data(), starts[g].size() * sizeof(int64_t));
+    }
+  }
+};
+
+// Validates the images and builds the descriptor tables of every group.
+adct_status build_tables(adct_context* ctx, const adct_image* imgs, int32_t n, int need, bool coef_only, int32_t cpb,
+                         Tables& t) {
+  if (n < 0) return fail(ctx, ADCT_ERR_INVALID_ARG, "negative image count");
+  if (n > 0 && !imgs) return fail(ctx, ADCT_ERR_INVALID_ARG, "imgs is NULL");
+  for (int g = 0; g < kGroups; ++g) {
+    t.planes[g].clear();
+    t.starts[g].assign(1, 0);
+  }
+  t.nplanes = 0;
+  t.blocks = 0;
+  PlaneDesc tmp[1];
+  for (int32_t m = 0; m < n; ++m) {
+    const adct_image& im = imgs[m];
+    const char* why = "";
+    const adct_status st = check_image(im, need, coef_only, &why);
+    if (st != ADCT_OK) return fail(ctx, st, std::string(why) + " (image " + std::to_string(m) + ")");
+    const int64_t nb = blocks_of(im);
+    const bool inter = im.layout == ADCT_LAYOUT_INTERLEAVED && !coef_only;
+    const int32_t parts = inter ? 1 : im.channels;
+    for (int32_t c = 0; c < parts; ++c) {
+      adct_image one = im;
+      int32_t cnt = 0;
+      if (!inter) {  // one planar plane at a time
+        one.channels = 1;
+        one.src = im.src ? im.src + (int64_t)c * im.plane_stride : nullptr;
+        one.dst = im.dst ? im.dst + (int64_t)c * im.plane_stride : nullptr;
+        one.coef = im.coef ? im.coef + (int64_t)c * nb * cpb : nullptr;
+      }
+      const int g = describe_image(one, cpb, coef_only, t.nplanes + c, tmp, &cnt);
+      t.planes[g].push_back(tmp[0]);
+      t.starts[g].push_back(t.starts[g].back() + nb);
+    }
+    t.nplanes += im.channels;
+    t.blocks += nb * im.channels;
+  }
+  t.serialise();
+  return ADCT_OK;
 }
 
 // Finds a slot whose device copy already holds exactly this table (a batch
@@ -250,14 +344,10 @@ void fill_table(void* host, const std::vector<PlaneDesc>& planes, const std::vec
 // as is, with no upload.  Only same-stream reuse is allowed, so that the slot's
 // `done` event, recorded after the new kernel, still covers every earlier
 // reader before the slot is ever overwritten.
-Slot* find_cached_slot(adct_context* ctx, const std::vector<PlaneDesc>& planes, const std::vector<int64_t>& starts,
-                       cudaStream_t stream) {
-  const size_t pb = planes.size() * sizeof(PlaneDesc), bytes = pb + starts.size() * sizeof(int64_t);
+Slot* find_cached_slot(adct_context* ctx, const std::vector<uint8_t>& blob, cudaStream_t stream) {
   for (Slot& s : ctx->slots) {
-    if (s.bytes != bytes || !s.host || s.stream != stream) continue;
-    if (std::memcmp(s.host, planes.data(), pb) == 0 &&
-        std::memcmp((const char*)s.host + pb, starts.data(), starts.size() * sizeof(int64_t)) == 0)
-      return &s;
+    if (s.bytes != blob.size() || !s.host || s.stream != stream) continue;
+    if (std::memcmp(s.host, blob.data(), blob.size()) == 0) return &s;
   }
   return nullptr;
 }
@@ -323,7 +413,32 @@ int need_for_kind(int kind) {
   }
 }
 
-// Validates, uploads the descriptor table through a workspace slot and launches.
+// One launch per non-empty group of t, whose tables are at dev (t.blob's layout).
+// Under stream capture (timed = false) no timing events are recorded.
+adct_status launch_groups(adct_context* ctx, CodecLaunch cl, const Tables& t, const char* dev, const LaunchShape& shape,
+                          cudaStream_t stream, bool timed = true) {
+  for (int g = 0; g < kGroups; ++g) {
+    if (t.total(g) == 0) continue;
+    cl.planes = (const PlaneDesc*)(dev + t.off_planes[g]);
+    cl.starts = (const int64_t*)(dev + t.off_starts[g]);
+    cl.nplanes = (int32_t)t.planes[g].size();
+    cl.total = t.total(g);
+    cl.nch = kGroupNch[g];
+    cl.edge = kGroupEdge[g];
+    cudaError_t e;
+    if (timed) {
+      TimedLaunch tl(ctx, stream);
+      e = launch_codec(cl, shape, ctx->sm_count, stream);
+      tl.done();
+    } else {
+      e = launch_codec(cl, shape, ctx->sm_count, stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "codec kernel launch");
+  }
+  return ADCT_OK;
+}
+
+// Validates, uploads the descriptor tables through a workspace slot and launches.
 adct_status run_codec(adct_context* ctx, const adct_image* imgs, int32_t n, const adct_quant* quant, int kind,
                       cudaStream_t stream, const LaunchShape& shape, unsigned long long* sse = nullptr) {
   if (!ctx) return ADCT_ERR_INVALID_ARG;
@@ -342,35 +457,28 @@ adct_status run_codec(adct_context* ctx, const adct_image* imgs, int32_t n, cons
   if (packed && kind == K_QUANTISE)
     return fail(ctx, ADCT_ERR_UNSUPPORTED, "the packed zonal layout is written by adct_roundtrip, not adct_quantise");
   if (packed && kind == K_INVERSE) cl.qmode = QM_ZONAL_ZZ;
-  std::vector<PlaneDesc> planes;
-  std::vector<int64_t> starts;
-  st = build_planes(ctx, imgs, n, need_for_kind(kind), planes, starts, packed ? quant->r : 64);
+  Tables t;
+  st = build_tables(ctx, imgs, n, need_for_kind(kind), kind == K_QUANTISE, packed ? quant->r : 64, t);
   if (st != ADCT_OK) return st;
-  cl.total = starts.back();
-  if (cl.total == 0) return ADCT_OK;
+  if (t.blocks == 0) return ADCT_OK;
   if (kind == K_QUANTISE && quant->mode == ADCT_Q_NONE) return ADCT_OK;  // identity
   DeviceGuard guard(ctx->device);
-  const size_t bytes = table_bytes(planes.size());
-  Slot* slot = find_cached_slot(ctx, planes, starts, stream);
+  const size_t bytes = t.blob.size();
+  Slot* slot = find_cached_slot(ctx, t.blob, stream);
   if (!slot) {
     st = acquire_slot(ctx, bytes, &slot);
     if (st != ADCT_OK) return st;
-    fill_table(slot->host, planes, starts);
+    std::memcpy(slot->host, t.blob.data(), bytes);
     ADCT_CUDA(ctx, cudaMemcpyAsync(slot->dev, slot->host, bytes, cudaMemcpyHostToDevice, stream));
     ADCT_CUDA(ctx, cudaEventRecord(slot->uploaded, stream));
     slot->bytes = bytes;
   }
-  cl.planes = (const PlaneDesc*)slot->dev;
-  cl.starts = (const int64_t*)((char*)slot->dev + planes.size() * sizeof(PlaneDesc));
-  cl.nplanes = (int32_t)planes.size();
   if (kind == K_RT_SSE) {
     cl.sse = sse;
-    ADCT_CUDA(ctx, cudaMemsetAsync(sse, 0, planes.size() * sizeof(unsigned long long), stream));
+    ADCT_CUDA(ctx, cudaMemsetAsync(sse, 0, (size_t)t.nplanes * sizeof(unsigned long long), stream));
   }
-  TimedLaunch tl(ctx, stream);
-  cudaError_t e = launch_codec(cl, shape, ctx->sm_count, stream);
-  tl.done();
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "codec kernel launch");
+  st = launch_groups(ctx, cl, t, (const char*)slot->dev, shape, stream);
+  if (st != ADCT_OK) return st;
   ADCT_CUDA(ctx, cudaEventRecord(slot->done, stream));
   slot->pending = true;
   slot->stream = stream;
@@ -408,7 +516,7 @@ std::string graph_key(const adct_image* imgs, int32_t n, const adct_quant* q, in
   put(q, sizeof *q);
   put(&n, sizeof n);
   for (int32_t m = 0; m < n; ++m) {
-    const int32_t dims[3] = {imgs[m].width, imgs[m].height, imgs[m].channels};
+    const int32_t dims[4] = {imgs[m].width, imgs[m].height, imgs[m].channels, imgs[m].layout};
     put(dims, sizeof dims);
   }
   return k;
@@ -588,11 +696,15 @@ adct_status adct_quality_dct(adct_context* ctx, const adct_image* imgs, int32_t 
   if (r < 0 || r > 64) return fail(ctx, ADCT_ERR_INVALID_ARG, "r outside 0..64");
   if (n > 0 && !sse) return fail(ctx, ADCT_ERR_INVALID_ARG, "sse is NULL");
   if ((uintptr_t)sse % 8) return fail(ctx, ADCT_ERR_ALIGN, "sse must be 8-byte aligned");
-  std::vector<PlaneDesc> planes;
-  std::vector<int64_t> starts;
-  adct_status st = build_planes(ctx, imgs, n, NEED_SRC, planes, starts);
+  for (int32_t m = 0; m < n && imgs; ++m)
+    if (imgs[m].layout != ADCT_LAYOUT_PLANAR || imgs[m].width % 8 || imgs[m].height % 8)
+      return fail(ctx, ADCT_ERR_UNSUPPORTED, "the DCT comparator takes planar images with sides multiple of 8");
+  Tables t;
+  adct_status st = build_tables(ctx, imgs, n, NEED_SRC, false, 64, t);
   if (st != ADCT_OK) return st;
-  if (starts.back() == 0) return ADCT_OK;
+  if (t.blocks == 0) return ADCT_OK;
+  const std::vector<PlaneDesc>& planes = t.planes[0];
+  const std::vector<int64_t>& starts = t.starts[0];
   // the orthonormal DCT-II matrix and the zig-zag zonal mask
   float c[64];
   for (int k = 0; k < 8; ++k)
@@ -605,20 +717,20 @@ adct_status adct_quality_dct(adct_context* ctx, const adct_image* imgs, int32_t 
     if (rank[k] < r) mask |= 1ull << k;
   DeviceGuard guard(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t bytes = table_bytes(planes.size());
-  Slot* slot = find_cached_slot(ctx, planes, starts, s);
+  const size_t bytes = t.blob.size();
+  Slot* slot = find_cached_slot(ctx, t.blob, s);
   if (!slot) {
     st = acquire_slot(ctx, bytes, &slot);
     if (st != ADCT_OK) return st;
-    fill_table(slot->host, planes, starts);
+    std::memcpy(slot->host, t.blob.data(), bytes);
     ADCT_CUDA(ctx, cudaMemcpyAsync(slot->dev, slot->host, bytes, cudaMemcpyHostToDevice, s));
     ADCT_CUDA(ctx, cudaEventRecord(slot->uploaded, s));
     slot->bytes = bytes;
   }
   ADCT_CUDA(ctx, cudaMemsetAsync(sse, 0, planes.size() * sizeof(uint64_t), s));
   TimedLaunch tl(ctx, s);
-  cudaError_t e = launch_dct_quality((const PlaneDesc*)slot->dev,
-                                     (const int64_t*)((char*)slot->dev + planes.size() * sizeof(PlaneDesc)),
+  cudaError_t e = launch_dct_quality((const PlaneDesc*)((const char*)slot->dev + t.off_planes[0]),
+                                     (const int64_t*)((const char*)slot->dev + t.off_starts[0]),
                                      (int32_t)planes.size(), starts.back(), c, mask, (unsigned long long*)sse,
                                      ctx->sm_count, s);
   tl.done();
@@ -674,16 +786,14 @@ adct_status adct_roundtrip_graph(adct_context* ctx, const adct_image* imgs, int3
   st = build_quant(ctx, quant, true, cl.qp, cl.evenq);
   if (st != ADCT_OK) return st;
   cl.qmode = quant->mode;
-  std::vector<PlaneDesc> planes;
-  std::vector<int64_t> starts;
-  st = build_planes(ctx, imgs, n, need_for_kind(kind), planes, starts, coef_per_block(quant));
+  Tables t;
+  st = build_tables(ctx, imgs, n, need_for_kind(kind), false, coef_per_block(quant), t);
   if (st != ADCT_OK) return st;
-  cl.total = starts.back();
-  if (cl.total == 0) return ADCT_OK;
+  if (t.blocks == 0) return ADCT_OK;
   DeviceGuard guard(ctx->device);
   const std::string key = graph_key(imgs, n, quant, kind, ctx->shape);
   auto it = ctx->graphs.find(key);
-  const size_t bytes = table_bytes(planes.size());
+  const size_t bytes = t.blob.size();
   if (it == ctx->graphs.end()) {
     GraphEntry g;
     g.bytes = bytes;
@@ -697,15 +807,12 @@ adct_status adct_roundtrip_graph(adct_context* ctx, const adct_image* imgs, int3
       return fail(ctx, ADCT_ERR_OOM, "graph workspace cudaMallocHost failed");
     }
     ADCT_CUDA(ctx, cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming));
-    cl.planes = (const PlaneDesc*)g.dev;
-    cl.starts = (const int64_t*)((char*)g.dev + planes.size() * sizeof(PlaneDesc));
-    cl.nplanes = (int32_t)planes.size();
     cudaStream_t cs = ctx->capture_stream;
     ADCT_CUDA(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     cudaError_t e1 = cudaMemcpyAsync(g.dev, g.host, bytes, cudaMemcpyHostToDevice, cs);
-    cudaError_t e2 = launch_codec(cl, ctx->shape, ctx->sm_count, cs);
+    const adct_status s2 = launch_groups(ctx, cl, t, (const char*)g.dev, ctx->shape, cs, false);
     cudaError_t e3 = cudaStreamEndCapture(cs, &g.graph);
-    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+    if (e1 != cudaSuccess || s2 != ADCT_OK || e3 != cudaSuccess) {
       cudaGetLastError();
       if (g.graph) cudaGraphDestroy(g.graph);
       cudaEventDestroy(g.done);
@@ -723,7 +830,7 @@ adct_status adct_roundtrip_graph(adct_context* ctx, const adct_image* imgs, int3
     ADCT_CUDA(ctx, cudaEventSynchronize(g.done));
     g.pending = false;
   }
-  fill_table(g.host, planes, starts);
+  std::memcpy(g.host, t.blob.data(), bytes);
   TimedLaunch tl(ctx, (cudaStream_t)stream);
   cudaError_t eg = cudaGraphLaunch(g.exec, (cudaStream_t)stream);
   tl.done();
@@ -797,10 +904,12 @@ adct_status adct_roundtrip_host(adct_context* ctx, const adct_image* himgs, int3
   // Host-side validation up front (shapes and pointers); device alignment is ours.
   for (int32_t m = 0; m < n; ++m) {
     const adct_image& im = himgs[m];
+    if (im.layout != ADCT_LAYOUT_PLANAR)
+      return fail(ctx, ADCT_ERR_UNSUPPORTED, "host buffers: planar images only (image " + std::to_string(m) + ")");
     if (im.width <= 0 || im.height <= 0 || im.width % 8 || im.height % 8 || im.width > 65536 || im.height > 65536 ||
         im.channels < 1 || im.pitch < im.width || (im.channels > 1 && im.plane_stride < im.pitch * im.height) ||
         !im.src)
-      return fail(ctx, ADCT_ERR_SHAPE, "bad host image " + std::to_string(m));
+      return fail(ctx, ADCT_ERR_SHAPE, "bad host image " + std::to_string(m) + " (sides multiples of 8)");
   }
   DeviceGuard guard(ctx->device);
   // chunk boundaries over whole images
@@ -1025,7 +1134,7 @@ namespace {
 
 constexpr int kNoAllocPlanes = ADCT_NOALLOC_MAX_PLANES;
 constexpr size_t kNoAllocTable = kNoAllocPlanes * sizeof(PlaneDesc);
-constexpr size_t kNoAllocBytes = kNoAllocTable + (kNoAllocPlanes + 1) * sizeof(int64_t);
+constexpr size_t kNoAllocBytes = kNoAllocTable + (kNoAllocPlanes + kGroups) * sizeof(int64_t);
 
 // Held by every device that loads the library, until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -1069,15 +1178,6 @@ adct_status noalloc_device(int dev, void** scratch, int* sm_count) {
   return ADCT_OK;
 }
 
-bool noalloc_bad_image(const adct_image& im, bool need_coef, bool need_dst) {
-  if (im.width <= 0 || im.height <= 0 || im.width % 8 || im.height % 8 || im.width > 65536 || im.height > 65536)
-    return true;
-  if (im.channels < 1 || im.reserved != 0 || im.pitch < im.width) return true;
-  if (im.channels > 1 && im.plane_stride < im.pitch * im.height) return true;
-  if (!im.src || (need_coef && !im.coef) || (need_dst && !im.dst)) return true;
-  return false;
-}
-
 }  // namespace
 
 extern "C" adct_status adct_roundtrip_noalloc(const adct_image* imgs, int32_t n, const adct_quant* quant,
@@ -1092,44 +1192,47 @@ extern "C" adct_status adct_roundtrip_noalloc(const adct_image* imgs, int32_t n,
   if (st != ADCT_OK) return st;
   cl.qmode = quant->mode;
 
-  // Descriptor table built on the stack: nothing is allocated.
+  // Descriptor tables built on the stack: nothing is allocated.  The groups
+  // (pixel layout classes) are laid out one after the other, all planes
+  // first, then each group's flat-index prefix.
   struct {
     PlaneDesc planes[kNoAllocPlanes];
-    int64_t starts[kNoAllocPlanes + 1];
+    int64_t starts[kNoAllocPlanes + kGroups];
   } table;
   static_assert(sizeof(table) == kNoAllocBytes, "table layout matches the device array");
-  int32_t np = 0;
-  int64_t total = 0;
+  const int need = NEED_SRC | (want_coef ? NEED_COEF : 0) | (want_dst ? NEED_DST : 0);
+  const int32_t cpb = coef_per_block(quant);
+  int32_t planes_total = 0;
   for (int32_t m = 0; m < n; ++m) {
     const adct_image& im = imgs[m];
     if ((im.coef != nullptr) != want_coef || (im.dst != nullptr) != want_dst) return ADCT_ERR_INVALID_ARG;
-    if (noalloc_bad_image(im, want_coef, want_dst)) {
-      const bool shape = im.width <= 0 || im.height <= 0 || im.width % 8 || im.height % 8 || im.width > 65536 ||
-                         im.height > 65536 || im.pitch < im.width ||
-                         (im.channels > 1 && im.plane_stride < im.pitch * im.height);
-      return shape ? ADCT_ERR_SHAPE : ADCT_ERR_INVALID_ARG;
-    }
-    if ((uintptr_t)im.src % 8 || (uintptr_t)im.dst % 8 || im.pitch % 8 || (im.channels > 1 && im.plane_stride % 8) ||
-        (uintptr_t)im.coef % 16)
-      return ADCT_ERR_ALIGN;
-    if (np + im.channels > kNoAllocPlanes) return ADCT_ERR_TOO_LARGE;
-    const int32_t wb = im.width / 8, hb = im.height / 8;
-    const int64_t nb = (int64_t)wb * hb;
-    for (int32_t c = 0; c < im.channels; ++c) {
-      PlaneDesc& d = table.planes[np];
-      d.src = im.src + (int64_t)c * im.plane_stride;
-      d.dst = im.dst ? im.dst + (int64_t)c * im.plane_stride : nullptr;
-      d.coef = im.coef ? im.coef + (int64_t)c * nb * coef_per_block(quant) : nullptr;
-      d.pitch = im.pitch;
-      d.first = total;
-      d.wb = wb;
-      d.hb = hb;
-      table.starts[np] = total;
-      ++np;
-      total += nb;
-    }
+    const char* why = "";
+    st = check_image(im, need, false, &why);
+    if (st != ADCT_OK) return st;
+    planes_total += im.layout == ADCT_LAYOUT_INTERLEAVED ? 1 : im.channels;
+    if (planes_total > kNoAllocPlanes) return ADCT_ERR_TOO_LARGE;
   }
-  table.starts[np] = total;
+  int32_t np = 0, gfirst[kGroups], gcount[kGroups];
+  for (int g = 0; g < kGroups; ++g) {  // one pass per group keeps each group's descriptors together
+    gfirst[g] = np;
+    int32_t pid = 0;
+    for (int32_t m = 0; m < n; ++m) {
+      if (group_of(imgs[m], false) == g) describe_image(imgs[m], cpb, false, pid, table.planes, &np);
+      pid += imgs[m].channels;
+    }
+    gcount[g] = np - gfirst[g];
+  }
+  // prefixes: group g's at starts[gfirst[g] + g .. gfirst[g] + g + gcount[g]]
+  for (int g = 0; g < kGroups; ++g) {
+    int64_t total = 0;
+    int64_t* st0 = table.starts + gfirst[g] + g;
+    for (int32_t k = 0; k < gcount[g]; ++k) {
+      const PlaneDesc& d = table.planes[gfirst[g] + k];
+      st0[k] = total;
+      total += (int64_t)d.wb * d.hb;
+    }
+    st0[gcount[g]] = total;
+  }
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -1140,9 +1243,9 @@ extern "C" adct_status adct_roundtrip_noalloc(const adct_image* imgs, int32_t n,
   int sm_count = 0;
   st = noalloc_device(dev, &scratch, &sm_count);
   if (st != ADCT_OK) return st;
-  // planes at offset 0, starts right after the planes of this call
+  // planes at offset 0, the groups' prefixes right after them
   const size_t plane_bytes = (size_t)np * sizeof(PlaneDesc);
-  const size_t start_bytes = (size_t)(np + 1) * sizeof(int64_t);
+  const size_t start_bytes = (size_t)(np + kGroups) * sizeof(int64_t);
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemcpyAsync(scratch, table.planes, plane_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync((char*)scratch + plane_bytes, table.starts, start_bytes, cudaMemcpyHostToDevice, s) !=
@@ -1150,14 +1253,19 @@ extern "C" adct_status adct_roundtrip_noalloc(const adct_image* imgs, int32_t n,
     cudaGetLastError();
     return ADCT_ERR_CUDA;
   }
-  cl.planes = (const PlaneDesc*)scratch;
-  cl.starts = (const int64_t*)((char*)scratch + plane_bytes);
-  cl.nplanes = np;
-  cl.total = total;
   const LaunchShape shape{128, 0, 1};
-  if (launch_codec(cl, shape, sm_count, s) != cudaSuccess) {
-    cudaGetLastError();
-    return ADCT_ERR_CUDA;
+  for (int g = 0; g < kGroups; ++g) {
+    if (gcount[g] == 0) continue;
+    cl.planes = (const PlaneDesc*)scratch + gfirst[g];
+    cl.starts = (const int64_t*)((char*)scratch + plane_bytes) + gfirst[g] + g;
+    cl.nplanes = gcount[g];
+    cl.total = table.starts[gfirst[g] + g + gcount[g]];
+    cl.nch = kGroupNch[g];
+    cl.edge = kGroupEdge[g];
+    if (launch_codec(cl, shape, sm_count, s) != cudaSuccess) {
+      cudaGetLastError();
+      return ADCT_ERR_CUDA;
+    }
   }
   return ADCT_OK;
 }

@@ -49,16 +49,20 @@ KernelFn pick_kernel(int kind, int qmode, bool evenq) {
 }  // namespace
 
 namespace {
-int warp_smem(int kind) {
+template <int NCH>
+int warp_smem_n(int kind) {
   switch (kind) {
-    case K_FORWARD: return SmemPlan<K_FORWARD>::warp;
-    case K_QUANTISE: return SmemPlan<K_QUANTISE>::warp;
-    case K_INVERSE: return SmemPlan<K_INVERSE>::warp;
-    case K_RT_FULL: return SmemPlan<K_RT_FULL>::warp;
-    case K_RT_PIX: return SmemPlan<K_RT_PIX>::warp;
-    case K_RT_SSE: return SmemPlan<K_RT_SSE>::warp;
-    default: return SmemPlan<K_RT_COEF>::warp;
+    case K_FORWARD: return SmemPlan<K_FORWARD, NCH>::warp;
+    case K_QUANTISE: return SmemPlan<K_QUANTISE, NCH>::warp;
+    case K_INVERSE: return SmemPlan<K_INVERSE, NCH>::warp;
+    case K_RT_FULL: return SmemPlan<K_RT_FULL, NCH>::warp;
+    case K_RT_PIX: return SmemPlan<K_RT_PIX, NCH>::warp;
+    case K_RT_SSE: return SmemPlan<K_RT_SSE, NCH>::warp;
+    default: return SmemPlan<K_RT_COEF, NCH>::warp;
   }
+}
+int warp_smem(int kind, int nch) {
+  return nch == 3 ? warp_smem_n<3>(kind) : nch == 4 ? warp_smem_n<4>(kind) : warp_smem_n<1>(kind);
 }
 }  // namespace
 
@@ -69,8 +73,8 @@ int warp_smem(int kind) {
 // the kernels that use more than 128 registers.
 int default_ctas_per_sm(int kind, int qmode) { return (kind == K_RT_COEF && qmode != QM_ZONAL_ZZ) ? 3 : 4; }
 
-size_t codec_smem_bytes(const LaunchShape& shape, int kind) {
-  return (size_t)(shape.threads / 32) * warp_smem(kind);
+size_t codec_smem_bytes(const LaunchShape& shape, int kind, int nch) {
+  return (size_t)(shape.threads / 32) * warp_smem(kind, nch);
 }
 
 int codec_grid(const LaunchShape& shape, int sm_count, int64_t total) {
@@ -83,7 +87,13 @@ int codec_grid(const LaunchShape& shape, int sm_count, int64_t total) {
 cudaError_t launch_codec(const CodecLaunch& c, const LaunchShape& shape, int sm_count, cudaStream_t stream) {
   if (c.total <= 0) return cudaSuccess;
   KernelFn fn = nullptr;
-  if (c.qmode == QM_ZONAL || c.qmode == QM_ZONAL_ZZ) {
+  if (c.nch == 3 || c.nch == 4) {
+    fn = pick_interleaved_kernel(c.kind, c.qmode, c.evenq, c.nch);
+    if (!fn) return cudaErrorInvalidValue;
+  } else if (c.edge) {
+    fn = pick_edge_kernel(c.kind, c.qmode, c.evenq);
+    if (!fn) return cudaErrorInvalidValue;
+  } else if (c.qmode == QM_ZONAL || c.qmode == QM_ZONAL_ZZ) {
     const int zs = zone_for(c.qp.r);
     if (zs <= kZoneLoMax) fn = pick_zonal_kernel_lo(c.kind, c.qmode, zs);
     else if (zs <= kZoneHiMax) fn = pick_zonal_kernel_hi(c.kind, c.qmode, zs);
@@ -91,7 +101,7 @@ cudaError_t launch_codec(const CodecLaunch& c, const LaunchShape& shape, int sm_
   if (!fn) fn = pick_kernel(c.kind, c.qmode, c.evenq);
   if (!fn) return cudaErrorInvalidValue;
   if (shape.threads < 32 || shape.threads > kMaxThreads || shape.threads % 32) return cudaErrorInvalidValue;
-  const size_t smem = codec_smem_bytes(shape, c.kind);
+  const size_t smem = codec_smem_bytes(shape, c.kind, c.nch);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -115,9 +115,18 @@ __device__ __forceinline__ const uint8_t* src_of(const PlaneDesc* d) {
 __device__ __forceinline__ uint8_t* dst_of(const PlaneDesc* d) {
   return (uint8_t*)__ldg((const unsigned long long*)&d->dst);
 }
-__device__ __forceinline__ int16_t* coef_of(const PlaneDesc* d, const Pos& q) {
+// Coefficients of block (by, bx) of channel ch (always 0 for a planar plane).
+__device__ __forceinline__ int16_t* coef_of(const PlaneDesc* d, const Pos& q, int ch = 0) {
   const int16_t* c = (const int16_t*)__ldg((const unsigned long long*)&d->coef);
-  return (int16_t*)c + ((int64_t)q.by * __ldg(&d->wb) + q.bx) * 64;
+  return (int16_t*)c + ch * __ldg(&d->cstride) + ((int64_t)q.by * __ldg(&d->wb) + q.bx) * 64;
+}
+// Valid pixel columns and rows of a block (8 inside the image; 1..8 in the
+// last block column / row of an image whose side is not a multiple of 8).
+__device__ __forceinline__ int valid_cols(const PlaneDesc* d, const Pos& q) {
+  return q.bx + 1 == (uint32_t)__ldg(&d->wb) ? __ldg(&d->ew) : 8;
+}
+__device__ __forceinline__ int valid_rows(const PlaneDesc* d, const Pos& q) {
+  return q.by + 1 == (uint32_t)__ldg(&d->hb) ? __ldg(&d->eh) : 8;
 }
 
 // Lane stride, in int16, of the packed staging: r, padded by 2 when r is a
@@ -125,9 +134,9 @@ __device__ __forceinline__ int16_t* coef_of(const PlaneDesc* d, const Pos& q) {
 // distinct banks (an odd word stride, or an odd value stride).
 __device__ __forceinline__ int zz_stride(int r) { return r + ((r & 3) == 0 ? 2 : 0); }
 
-__device__ __forceinline__ int16_t* coef_of_zz(const PlaneDesc* d, const Pos& q, int r) {
+__device__ __forceinline__ int16_t* coef_of_zz(const PlaneDesc* d, const Pos& q, int r, int ch = 0) {
   const int16_t* c = (const int16_t*)__ldg((const unsigned long long*)&d->coef);
-  return (int16_t*)c + ((int64_t)q.by * __ldg(&d->wb) + q.bx) * r;
+  return (int16_t*)c + ch * __ldg(&d->cstride) + ((int64_t)q.by * __ldg(&d->wb) + q.bx) * r;
 }
 
 // Plane cursor of one lane: the flat index only grows (by 32 per tile), so the
@@ -180,20 +189,34 @@ constexpr int kTile = 32;
 // i + 1 .. i + stages - 1 are in flight.  Two stages measured best: a third
 // stage for pixel input (4 KB in flight per warp) made the kernels with the
 // least arithmetic per block slower by up to 20 % at the same occupancy.
-template <int KIND>
+//
+// NCH > 1 (interleaved images): a tile is 32 pixel positions of NCH channels;
+// its input stage holds the 8 rows of 32 x 8 NCH interleaved bytes, and the
+// reconstructed pixels are written back into the same stage (a channel's
+// bytes once that channel's block is in registers) before the warp stores
+// them.  The inverse from coefficients uses the stage only for that.
+template <int KIND, int NCH = 1>
 struct SmemPlan {
   static constexpr int stages = 2;
-  static constexpr int in_stage = KindTraits<KIND>::in_pix ? 2048 : 4096;  // one 32-block tile of input
+  static constexpr int in_stage =
+      (KindTraits<KIND>::in_pix || NCH > 1) ? 2048 * NCH : 4096;  // one 32-block (or 32-position) tile of input
   static constexpr int out_stage = KindTraits<KIND>::write_coef ? kTileBytesOut : 0;
   static constexpr int warp = stages * in_stage + out_stage;
 };
 
 // Arithmetic of one 8x8 block: read its input from the input stage, quantise,
 // stage or store q, dequantise, invert and store the pixels.
-template <int KIND, int QMODE, bool EVENQ, int ZS>
-__device__ __forceinline__ uint32_t block_step(const uint8_t* __restrict__ in, uint8_t* __restrict__ stage_out,
-                                               const PlaneDesc* __restrict__ planes, const Pos& pos, int stage_coef,
-                                               const QuantParams& qp, int lane) {
+//
+// NCH > 1: channel ch of an interleaved image; the pixel bytes of lane l's
+// position in row i of the stage are at (i * 32 + l) * 8 NCH + NCH * j + ch.
+//
+// EDGE: the launch may contain blocks on the right or bottom edge of an image
+// whose side is not a multiple of 8 (compiled out of the launches that have
+// none).
+template <int KIND, int QMODE, bool EVENQ, int ZS, int NCH, bool EDGE>
+__device__ __forceinline__ uint32_t block_step(uint8_t* __restrict__ in, uint8_t* __restrict__ stage_out,
+                                               const PlaneDesc* __restrict__ planes, const Pos& pos, int ch,
+                                               int stage_coef, const QuantParams& qp, int lane) {
   using KT = KindTraits<KIND>;
   // With a zonal quantiser every coefficient beyond anti-diagonal ZS is zero
   // (the kept r fit in diagonals 0..ZS): known at compile time, so the forward
@@ -203,7 +226,7 @@ __device__ __forceinline__ uint32_t block_step(const uint8_t* __restrict__ in, u
   if (pos.plane < 0) return 0;
   const PlaneDesc* d = planes + pos.plane;
   int32_t v[64];
-  if (KT::in_pix) {
+  if (KT::in_pix && NCH == 1) {
     const uint2* st = (const uint2*)in;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -215,15 +238,32 @@ __device__ __forceinline__ uint32_t block_step(const uint8_t* __restrict__ in, u
       }
     }
     fwd2d(v);  // Z + 8192 e0 e0^T (raw pixels; the level shift lives in the constants)
+  } else if (KT::in_pix) {
+    const uint8_t* px = in + lane * 8 * NCH + ch;  // channel ch's bytes, NCH apart
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[8 * i + j] = px[i * 256 * NCH + NCH * j];
+    fwd2d(v);
   } else if (QMODE == QM_ZONAL_ZZ) {
     // packed input: the first r zig-zag coefficients of this block
     constexpr ZigZag zz = make_zigzag();
-    const int16_t* c = (const int16_t*)__ldg((const unsigned long long*)&d->coef) +
-                       ((int64_t)pos.by * __ldg(&d->wb) + pos.bx) * qp.r;
+    const int16_t* c = coef_of_zz(d, pos, qp.r, ch);
 #pragma unroll
     for (int k = 0; k < 64; ++k) v[k] = 0;
 #pragma unroll
     for (int t = 0; t < kZoneN; ++t) v[zz.pos[t]] = (t < qp.r) ? (int32_t)__ldg(c + t) : 0;
+  } else if (NCH > 1) {
+    // inverse into an interleaved image: this channel's block straight from memory
+    const int4* cp = (const int4*)coef_of(d, pos, ch);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int4 u = __ldg(cp + t);
+      v[8 * t + 0] = sext_lo16(u.x); v[8 * t + 1] = sext_hi16(u.x);
+      v[8 * t + 2] = sext_lo16(u.y); v[8 * t + 3] = sext_hi16(u.y);
+      v[8 * t + 4] = sext_lo16(u.z); v[8 * t + 5] = sext_hi16(u.z);
+      v[8 * t + 6] = sext_lo16(u.w); v[8 * t + 7] = sext_hi16(u.w);
+    }
   } else {
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
@@ -238,7 +278,7 @@ __device__ __forceinline__ uint32_t block_step(const uint8_t* __restrict__ in, u
   // ---- packed zonal output: the first r zig-zag coefficients, staged per lane ----
   if (QMODE == QM_ZONAL_ZZ && KT::write_coef) {
     constexpr ZigZag zz = make_zigzag();
-    int16_t* out = stage_coef ? (int16_t*)stage_out + lane * zz_stride(qp.r) : coef_of_zz(d, pos, qp.r);
+    int16_t* out = stage_coef ? (int16_t*)stage_out + lane * zz_stride(qp.r) : coef_of_zz(d, pos, qp.r, ch);
 #pragma unroll
     for (int t = 0; t < kZoneN; ++t) {
       const int k = zz.pos[t];
@@ -293,49 +333,115 @@ __device__ __forceinline__ uint32_t block_step(const uint8_t* __restrict__ in, u
       u.z = (int)pack16(q[4], q[5]);
       u.w = (int)pack16(q[6], q[7]);
       if (stage_coef) *(int4*)(stage_out + swz(lane, i)) = u;
-      else __stcs((int4*)coef_of(d, pos) + i, u);
+      else __stcs((int4*)coef_of(d, pos, ch) + i, u);
     }
   }
 
   // ---- inverse (8 column, then 8 row transposed butterflies) and output ----
+  // Blocks on the right or bottom edge of an image whose side is not a
+  // multiple of 8 store (and compare) only their valid rows and columns.
   uint32_t err = 0;
   if (KT::inv) {
     inv2d(v);
-    if (KT::sse) {
+    const int vc = EDGE ? valid_cols(d, pos) : 8, vr = EDGE ? valid_rows(d, pos) : 8;
+    if (KT::sse && NCH == 1) {
       // squared error against the input rows, still in the input stage
       const uint2* st = (const uint2*)in;
+      const uint32_t m0 = vc >= 4 ? 0xffffffffu : (1u << (8 * vc)) - 1u;
+      const uint32_t m1 = vc >= 8 ? 0xffffffffu : vc <= 4 ? 0u : (1u << (8 * (vc - 4))) - 1u;
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const uint2 x = st[i * 32 + lane];
-        const uint32_t e0 = __vabsdiffu4(pixels4(v[8 * i + 0], v[8 * i + 1], v[8 * i + 2], v[8 * i + 3]), x.x);
-        const uint32_t e1 = __vabsdiffu4(pixels4(v[8 * i + 4], v[8 * i + 5], v[8 * i + 6], v[8 * i + 7]), x.y);
-        err = __dp4a(e0, e0, err);
-        err = __dp4a(e1, e1, err);
+        const uint32_t e0 = __vabsdiffu4(pixels4(v[8 * i + 0], v[8 * i + 1], v[8 * i + 2], v[8 * i + 3]), x.x) & m0;
+        const uint32_t e1 = __vabsdiffu4(pixels4(v[8 * i + 4], v[8 * i + 5], v[8 * i + 6], v[8 * i + 7]), x.y) & m1;
+        if (i < vr) {
+          err = __dp4a(e0, e0, err);
+          err = __dp4a(e1, e1, err);
+        }
       }
-    } else {
+    } else if (KT::sse) {
+      const uint8_t* px = in + lane * 8 * NCH + ch;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+#pragma unroll
+        for (int j4 = 0; j4 < 2; ++j4) {
+          const uint32_t w = pixels4(v[8 * i + 4 * j4], v[8 * i + 4 * j4 + 1], v[8 * i + 4 * j4 + 2],
+                                     v[8 * i + 4 * j4 + 3]);
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int j = 4 * j4 + b;
+            const int e = (int)((w >> (8 * b)) & 0xffu) - (int)px[i * 256 * NCH + NCH * j];
+            if (i < vr && j < vc) err += (uint32_t)(e * e);
+          }
+        }
+      }
+    } else if (NCH == 1) {
       const int64_t pitch = __ldg(&d->pitch);
       uint8_t* o = dst_of(d) + (int64_t)(8 * pos.by) * pitch + 8 * pos.bx;
+      const bool edge = (vc < 8) | (vr < 8);
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         uint2 w;
         w.x = pixels4(v[8 * i + 0], v[8 * i + 1], v[8 * i + 2], v[8 * i + 3]);
         w.y = pixels4(v[8 * i + 4], v[8 * i + 5], v[8 * i + 6], v[8 * i + 7]);
-        __stcs((uint2*)(o + i * pitch), w);
+        if (!edge) {
+          __stcs((uint2*)(o + i * pitch), w);
+        } else if (i < vr) {
+          for (int j = 0; j < vc; ++j) o[i * pitch + j] = (uint8_t)((j < 4 ? w.x >> (8 * j) : w.y >> (8 * (j - 4))));
+        }
+      }
+    } else {
+      // interleaved: channel ch's bytes back into the stage, stored by the warp
+      uint8_t* px = in + lane * 8 * NCH + ch;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+#pragma unroll
+        for (int j4 = 0; j4 < 2; ++j4) {
+          const uint32_t w = pixels4(v[8 * i + 4 * j4], v[8 * i + 4 * j4 + 1], v[8 * i + 4 * j4 + 2],
+                                     v[8 * i + 4 * j4 + 3]);
+#pragma unroll
+          for (int b = 0; b < 4; ++b) px[i * 256 * NCH + NCH * (4 * j4 + b)] = (uint8_t)(w >> (8 * b));
+        }
       }
     }
   }
   return err;
 }
 
+// Store the reconstructed interleaved pixels of a 32-position tile from its
+// stage: lane l writes its 8 NCH bytes of each valid row (NCH 8-byte stores,
+// so the warp covers 256 NCH contiguous bytes per row), byte by byte on the
+// image's right edge.
+template <int NCH, bool EDGE>
+__device__ __forceinline__ void write_pixels_interleaved(const uint8_t* __restrict__ stage,
+                                                        const PlaneDesc* __restrict__ planes, const Pos& pos,
+                                                        int lane) {
+  if (pos.plane < 0) return;
+  const PlaneDesc* d = planes + pos.plane;
+  const int64_t pitch = __ldg(&d->pitch);
+  uint8_t* o = dst_of(d) + (int64_t)(8 * pos.by) * pitch + 8 * NCH * pos.bx;
+  const int vc = EDGE ? valid_cols(d, pos) : 8, vr = EDGE ? valid_rows(d, pos) : 8;
+  const uint8_t* sp = stage + lane * 8 * NCH;
+  for (int i = 0; i < vr; ++i) {
+    if (vc == 8) {
+#pragma unroll
+      for (int k = 0; k < NCH; ++k)
+        __stcs((uint2*)(o + i * pitch) + k, *(const uint2*)(sp + i * 256 * NCH + 8 * k));
+    } else {
+      for (int b = 0; b < NCH * vc; ++b) o[i * pitch + b] = sp[i * 256 * NCH + b];
+    }
+  }
+}
+
 // Write a staged 32-block half-tile of coefficients back with 512-byte warp
 // stores.  The blocks of a plane are contiguous in coef, so when every active
 // lane is in lane 0's plane the half-tile is one contiguous range.
 __device__ __forceinline__ void write_back(const uint8_t* __restrict__ stage_out, const PlaneDesc* __restrict__ planes,
-                                          const Pos& pos, int lane) {
+                                          const Pos& pos, int lane, int ch) {
   const bool active = pos.plane >= 0;
   const int plane0 = __shfl_sync(0xffffffffu, pos.plane, 0);
   const unsigned act = __ballot_sync(0xffffffffu, active);
-  int16_t* mine = active ? coef_of(planes + pos.plane, pos) : nullptr;
+  int16_t* mine = active ? coef_of(planes + pos.plane, pos, ch) : nullptr;
   // Instruction k moves bytes [512 k, 512 k + 512) of the half-tile: lane l
   // takes 16-byte chunk (l & 7) of block 4 k + (l >> 3), i.e. byte 512 k + 16 l;
   // in shared memory that chunk sits at one of two lane-specific offsets (the
@@ -370,11 +476,11 @@ __device__ __forceinline__ void write_back(const uint8_t* __restrict__ stage_out
 template <int NMAX>
 __device__ __forceinline__ void write_back_zz(const uint8_t* __restrict__ stage_out,
                                              const PlaneDesc* __restrict__ planes, const Pos& pos, int lane, int r,
-                                             uint32_t mh) {
+                                             uint32_t mh, int ch) {
   const bool active = pos.plane >= 0;
   const int plane0 = __shfl_sync(0xffffffffu, pos.plane, 0);
   const unsigned act = __ballot_sync(0xffffffffu, active);
-  int16_t* mine = active ? coef_of_zz(planes + pos.plane, pos, r) : nullptr;
+  int16_t* mine = active ? coef_of_zz(planes + pos.plane, pos, r, ch) : nullptr;
   const int16_t* st16 = (const int16_t*)stage_out;
   const bool padded = (r & 3) == 0;
   if (__all_sync(0xffffffffu, !active || pos.plane == plane0)) {
@@ -405,12 +511,12 @@ __device__ __forceinline__ void write_back_zz(const uint8_t* __restrict__ stage_
   }
 }
 
-template <int KIND, int QMODE, bool EVENQ, int ZS>
+template <int KIND, int QMODE, bool EVENQ, int ZS, int NCH = 1, bool EDGE = false>
 __global__ void __launch_bounds__(kMaxThreads, 3)
 k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts, int32_t nplanes, int64_t total,
         int64_t chunk, int stage_coef, unsigned long long* __restrict__ sse, const QuantParams qp) {
   using KT = KindTraits<KIND>;
-  using SP = SmemPlan<KIND>;
+  using SP = SmemPlan<KIND, NCH>;
   constexpr int S = SP::stages;
   extern __shared__ __align__(128) uint8_t smem[];
   const int lane = threadIdx.x & 31;
@@ -439,17 +545,37 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
 
   // Issue the asynchronous input copies of one tile into stage st (lanes past
   // the end of the chunk copy nothing; the group is committed regardless).
+  // Pixels: lane l's 8 NCH bytes of row i go to (i * 32 + l) * 8 NCH, so the
+  // warp's copies of one row cover 256 NCH contiguous bytes.  A block on the
+  // right or bottom edge of an image whose side is not a multiple of 8 is
+  // filled synchronously instead, replicating the last valid column and row.
   auto issue = [&](int st, const Pos& q) {
-    const uint32_t sa = smem_addr(wsm + st * SP::in_stage);
+    uint8_t* sp = wsm + st * SP::in_stage;
+    const uint32_t sa = smem_addr(sp);
     if (KT::in_pix) {
       if (q.plane >= 0) {
         const PlaneDesc* d = planes + q.plane;
         const int64_t pitch = __ldg(&d->pitch);
-        const uint8_t* src = src_of(d) + (int64_t)(8 * q.by) * pitch + 8 * q.bx;
+        const uint8_t* src = src_of(d) + (int64_t)(8 * q.by) * pitch + 8 * NCH * q.bx;
+        const int vc = EDGE ? valid_cols(d, q) : 8, vr = EDGE ? valid_rows(d, q) : 8;
+        if (vc == 8 && vr == 8) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) cp_async8(sa + (i * 32 + lane) * 8, src + i * pitch);
+          for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int k = 0; k < NCH; ++k) cp_async8(sa + ((i * 32 + lane) * NCH + k) * 8, src + i * pitch + 8 * k);
+        } else {
+          for (int i = 0; i < 8; ++i) {
+            const uint8_t* row = src + (int64_t)min(i, vr - 1) * pitch;
+            uint8_t* dst = sp + (i * 32 + lane) * 8 * NCH;
+            for (int j = 0; j < 8; ++j) {
+              const int x = min(j, vc - 1);
+#pragma unroll
+              for (int k = 0; k < NCH; ++k) dst[NCH * j + k] = row[NCH * x + k];
+            }
+          }
+        }
       }
-    } else if (QMODE != QM_ZONAL_ZZ) {
+    } else if (QMODE != QM_ZONAL_ZZ && NCH == 1) {
       // Coefficients: lane copies 16-byte chunk c of block b (512 contiguous
       // bytes per warp instruction when the tile lies in one plane).
       const int16_t* mine = q.plane >= 0 ? coef_of(planes + q.plane, q) : nullptr;
@@ -466,8 +592,18 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
   // packed staging with padding: word w of a half-tile is in block w / (r / 2)
   const uint32_t zz_mh =
       (QMODE == QM_ZONAL_ZZ && qp.r >= 4) ? ((1u << 20) + (qp.r >> 1) - 1) / (uint32_t)(qp.r >> 1) : 0;
-  unsigned long long acc = 0;  // K_RT_SSE: this lane's error sum for plane acc_plane
+  // K_RT_SSE: this lane's error sums for the channels of descriptor acc_plane
+  unsigned long long acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
   int acc_plane = -1;
+  auto flush = [&]() {
+    if (acc_plane < 0) return;
+    const int pid = __ldg(&planes[acc_plane].plane_id);
+    atomicAdd(sse + pid, acc0);
+    if (NCH > 1) atomicAdd(sse + pid + 1, acc1);
+    if (NCH > 2) atomicAdd(sse + pid + 2, acc2);
+    if (NCH > 3) atomicAdd(sse + pid + 3, acc3);
+    acc0 = acc1 = acc2 = acc3 = 0;
+  };
   Pos ring[S - 1];  // positions of tiles i .. i + S - 2, whose copies are issued
 #pragma unroll
   for (int k = 0; k < S - 1; ++k) {
@@ -483,29 +619,40 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
     __syncwarp();
 
     const Pos pc = ring[0];
-    const uint32_t e = block_step<KIND, QMODE, EVENQ, ZS>(wsm + s * SP::in_stage, stage_out, planes, pc, stage_coef,
-                                                          qp, lane);
-    if (KT::sse && pc.plane >= 0) {
-      if (pc.plane != acc_plane) {  // one atomic per lane per plane it visits
-        if (acc_plane >= 0) atomicAdd(sse + acc_plane, acc);
-        acc_plane = pc.plane;
-        acc = 0;
+    uint8_t* stage = wsm + s * SP::in_stage;
+    if (KT::sse && pc.plane >= 0 && pc.plane != acc_plane) {  // one atomic per lane and channel per plane visited
+      flush();
+      acc_plane = pc.plane;
+    }
+    auto channel = [&](int ch) {
+      const uint32_t e =
+          block_step<KIND, QMODE, EVENQ, ZS, NCH, EDGE>(stage, stage_out, planes, pc, ch, stage_coef, qp, lane);
+      if (KT::sse) {
+        if (ch == 0) acc0 += e;
+        else if (ch == 1) acc1 += e;
+        else if (ch == 2) acc2 += e;
+        else acc3 += e;
       }
-      acc += e;
+      if (KT::write_coef && stage_coef) {
+        __syncwarp();
+        if (QMODE == QM_ZONAL_ZZ) write_back_zz<zone_count(ZS)>(stage_out, planes, pc, lane, qp.r, zz_mh, ch);
+        else write_back(stage_out, planes, pc, lane, ch);
+        __syncwarp();
+      }
+    };
+    if (NCH == 1) {
+      channel(0);
+    } else {
+#pragma unroll 1
+      for (int ch = 0; ch < NCH; ++ch) channel(ch);
     }
-
-    if (KT::write_coef && stage_coef) {
-      __syncwarp();
-      if (QMODE == QM_ZONAL_ZZ) write_back_zz<zone_count(ZS)>(stage_out, planes, pc, lane, qp.r, zz_mh);
-      else write_back(stage_out, planes, pc, lane);
-      __syncwarp();
-    }
+    if (NCH > 1 && KT::inv && !KT::sse) write_pixels_interleaved<NCH, EDGE>(stage, planes, pc, lane);
 #pragma unroll
     for (int k = 0; k + 1 < S - 1; ++k) ring[k] = ring[k + 1];
     ring[S - 2] = pl;
     if (++s == S) s = 0;
   }
-  if (KT::sse && acc_plane >= 0) atomicAdd(sse + acc_plane, acc);
+  if (KT::sse) flush();
   cp_async_wait<0>();
 }
 
@@ -520,6 +667,40 @@ KernelFn pick_zone(int kind, int qmode) {
     case K_RT_PIX: return k_codec<K_RT_PIX, QM_ZONAL, false, ZS>;
     case K_RT_SSE: return k_codec<K_RT_SSE, QM_ZONAL, false, ZS>;
     case K_INVERSE: return zz ? k_codec<K_INVERSE, QM_ZONAL_ZZ, false, ZS> : nullptr;
+    default: return nullptr;
+  }
+}
+
+// The full-zone kernels of one pixel layout / edge class (NCH channels per
+// descriptor, EDGE handling) for every kind that touches pixels; nullptr for
+// the coefficient-only quantiser.
+template <int KIND, int NCH, bool EDGE>
+KernelFn pick_full_mode(int qmode, bool evenq) {
+  switch (qmode) {
+    case QM_STEP:
+      return evenq ? k_codec<KIND, QM_STEP, true, 14, NCH, EDGE> : k_codec<KIND, QM_STEP, false, 14, NCH, EDGE>;
+    case QM_ZONAL: return k_codec<KIND, QM_ZONAL, false, 14, NCH, EDGE>;
+    case QM_STEP_ZONAL:
+      return evenq ? k_codec<KIND, QM_STEP_ZONAL, true, 14, NCH, EDGE>
+                   : k_codec<KIND, QM_STEP_ZONAL, false, 14, NCH, EDGE>;
+    case QM_ZONAL_ZZ:
+      return (KIND == K_RT_FULL || KIND == K_RT_COEF) ? k_codec<KIND, QM_ZONAL_ZZ, false, 14, NCH, EDGE>
+                                                       : k_codec<KIND, QM_ZONAL, false, 14, NCH, EDGE>;
+    default: return k_codec<KIND, QM_NONE, false, 14, NCH, EDGE>;
+  }
+}
+
+template <int NCH, bool EDGE>
+KernelFn pick_full(int kind, int qmode, bool evenq) {
+  switch (kind) {
+    case K_FORWARD: return k_codec<K_FORWARD, QM_NONE, false, 14, NCH, EDGE>;
+    case K_INVERSE:
+      return qmode == QM_ZONAL_ZZ ? k_codec<K_INVERSE, QM_ZONAL_ZZ, false, 14, NCH, EDGE>
+                                  : k_codec<K_INVERSE, QM_NONE, false, 14, NCH, EDGE>;
+    case K_RT_FULL: return pick_full_mode<K_RT_FULL, NCH, EDGE>(qmode, evenq);
+    case K_RT_PIX: return pick_full_mode<K_RT_PIX, NCH, EDGE>(qmode, evenq);
+    case K_RT_COEF: return pick_full_mode<K_RT_COEF, NCH, EDGE>(qmode, evenq);
+    case K_RT_SSE: return pick_full_mode<K_RT_SSE, NCH, EDGE>(qmode, evenq);
     default: return nullptr;
   }
 }

@@ -102,16 +102,26 @@ __host__ __device__ __forceinline__ void inv2d(const VI* in, V* v) {
 // One plane of the flattened block index.  Planes of a multi-channel image
 // are separate entries.  Block f of the plane (row-major over blocks) sits at
 // src + (8 * (f / wb)) * pitch + 8 * (f % wb); its coefficients at coef + 64 f.
+// One unit of the flat work index: a planar uint8 plane (the flat index counts
+// its 8x8 blocks), or an interleaved image of nch = 3 or 4 channels (the flat
+// index counts its 8x8 pixel positions, each carrying nch blocks).  Images
+// whose sides are not multiples of 8 are covered by ceil(side / 8) blocks; the
+// last block column holds ew valid pixel columns and the last block row eh
+// valid rows (1..8), the rest is the edge replicated.
 struct PlaneDesc {
   const uint8_t* src;
   uint8_t* dst;
-  int16_t* coef;
-  int64_t pitch;
-  int64_t first;  // flat index of the plane's block 0
-  int32_t wb;     // blocks per row
-  int32_t hb;     // block rows
+  int16_t* coef;    // channel 0's coefficients
+  int64_t pitch;    // bytes between pixel rows
+  int64_t cstride;  // int16 between the coefficient planes of consecutive channels
+  int32_t wb;       // blocks per row
+  int32_t hb;       // block rows
+  int32_t ew;       // valid pixel columns of the last block column
+  int32_t eh;       // valid pixel rows of the last block row
+  int32_t plane_id; // plane number of channel 0 in the call (per-plane outputs)
+  int32_t nch;      // 1: planar plane; 3, 4: interleaved channels
 };
-static_assert(sizeof(PlaneDesc) == 48, "descriptor layout");
+static_assert(sizeof(PlaneDesc) == 64, "descriptor layout");
 
 // Per-call quantiser constants, passed by value: they live in the kernel
 // parameter bank, so the fully unrolled per-position accesses are free

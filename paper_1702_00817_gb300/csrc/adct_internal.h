@@ -35,6 +35,8 @@ struct CodecLaunch {
   int qmode;                // QMode (quantiser applied by QUANTISE / RT kinds)
   bool evenq;               // the step table has an even step <= 16384 (tie correction needed)
   unsigned long long* sse;  // K_RT_SSE: per-plane sums of squared reconstruction error (device)
+  int nch;                  // 1: planar planes; 3 or 4: interleaved images
+  bool edge;                // some image has a side that is not a multiple of 8
   QuantParams qp;
 };
 
@@ -47,13 +49,18 @@ using KernelFn = void (*)(const PlaneDesc*, const int64_t*, int32_t, int64_t, in
 // kind / mode pair has no specialisation.
 KernelFn pick_zonal_kernel_lo(int kind, int qmode, int zs);
 KernelFn pick_zonal_kernel_hi(int kind, int qmode, int zs);
+// Kernels for interleaved images of nch = 3 or 4 channels
+// (adct_codec_interleaved.cu); nullptr for kinds without one.
+KernelFn pick_interleaved_kernel(int kind, int qmode, bool evenq, int nch);
+// Kernels for planar images with edge blocks (adct_codec_edge.cu).
+KernelFn pick_edge_kernel(int kind, int qmode, bool evenq);
 
 // Launches the integer codec kernel.  Returns cudaSuccess or the launch error.
 cudaError_t launch_codec(const CodecLaunch& c, const LaunchShape& shape, int sm_count, cudaStream_t stream);
 
 // Largest grid the persistent kernel uses for this shape (CTAs), and its dynamic shared memory.
 int codec_grid(const LaunchShape& shape, int sm_count, int64_t total);
-size_t codec_smem_bytes(const LaunchShape& shape, int kind);
+size_t codec_smem_bytes(const LaunchShape& shape, int kind, int nch = 1);
 
 // Exact-DCT comparator of the quality sweep: zonal round trip of every block
 // with the orthonormal 8x8 DCT-II in float32; per-plane squared error.

@@ -234,10 +234,14 @@ def test_empty_batch_is_a_no_op(codec):
 
 
 def test_argument_errors(codec):
-    src = torch.zeros((16, 20), dtype=torch.uint8, device=DEV)  # width not a multiple of 8
+    src = torch.zeros((16, 65544), dtype=torch.uint8, device=DEV)  # wider than 65536
     with pytest.raises(AdctError) as e:
         codec.roundtrip([Image(src, src.clone(), None)], make_quant(ADCT_Q_NONE))
     assert e.value.status == 2
+    src = torch.zeros((16, 20), dtype=torch.uint8, device=DEV)  # rows 20 bytes apart: not 8-byte aligned
+    with pytest.raises(AdctError) as e:
+        codec.roundtrip([Image(src, src.clone(), None)], make_quant(ADCT_Q_NONE))
+    assert e.value.status == 3
     src = torch.zeros((16, 16), dtype=torch.uint8, device=DEV)
     with pytest.raises(AdctError) as e:
         codec.roundtrip([Image(src, src.clone(), None)], make_quant(ADCT_Q_STEP, np.zeros(64)))
