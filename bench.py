@@ -9,7 +9,7 @@ quantiser settings: step tables Q_ij = 1 + floor(s (1 + i + j)) for s in
 {1, 4, 16} and zonal retention r in {1, 6, 10, 16, 64}.
 
 Prints one JSON line (rank 0).  Other workloads (--workload ragged | float |
-serving | quality | packed) print their own lines.  --impl reference times the CPU oracle on the
+serving | quality | packed | layout) print their own lines.  --impl reference times the CPU oracle on the
 host cores instead.
 """
 from __future__ import annotations
@@ -41,7 +41,7 @@ def parse():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["roundtrip", "ragged", "float", "serving", "quality", "packed"], default="roundtrip")
+    p.add_argument("--workload", choices=["roundtrip", "ragged", "float", "serving", "quality", "packed", "layout"], default="roundtrip")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--images", type=int, default=N_IMG)
@@ -517,6 +517,82 @@ def run_packed(args):
     return 0
 
 
+def run_layout(args):
+    """Pixel layouts on the fused round trip (step s = 4): 64 RGB 1080x1920
+    images interleaved (HWC) vs the same pixels as planar planes, and planar
+    1080x1917 images (an edge block column on every block row) vs 1080x1920."""
+    import torch
+
+    from paper_1702_00817_gb300 import _build, inputs
+    from paper_1702_00817_gb300.codec import ADCT_Q_STEP, Codec, Image, image_array, make_quant
+    d = Dist()
+    dev = torch.device("cuda", d.local)
+    torch.cuda.set_device(dev)
+    if d.rank == 0 or not _build.up_to_date():
+        _build.build()
+    d.barrier()
+    n, H, W = 64, 1080, 1920
+    codec = Codec(d.local)
+    lib, ctx = codec.lib, codec.ctx
+    stream = torch.cuda.current_stream(dev)
+    sh = ctypes.c_void_p(stream.cuda_stream)
+    q = make_quant(ADCT_Q_STEP, inputs.step_table(4))
+    peak, peak_kind = measured_peaks()
+    planar = torch.stack([inputs.synth_image_device(H, W, inputs.BASE_SEED + d.rank * n + k, 3, dev)
+                          for k in range(n)])  # [n, 3, H, W]
+    hwc = planar.permute(0, 2, 3, 1).contiguous()  # [n, H, W, 3], the same pixels
+    coef = torch.empty((n, 3, H // 8, W // 8, 8, 8), dtype=torch.int16, device=dev)
+    dst_p, dst_i = torch.empty_like(planar), torch.empty_like(hwc)
+    W2 = W - 3  # 1917: the last block column holds 5 valid columns
+    edge = planar[:, :, :, :W2]  # pitch stays 1920
+    dst_e = torch.empty_like(planar)[:, :, :, :W2]
+    forms = {
+        "planar_1080x1920x3": (image_array([Image(planar[k], dst_p[k], coef[k]) for k in range(n)]),
+                               n * 3 * (H // 8) * (W // 8)),
+        "interleaved_1080x1920x3": (image_array([Image(hwc[k], dst_i[k], coef[k], True) for k in range(n)]),
+                                    n * 3 * (H // 8) * (W // 8)),
+        "planar_1080x1917x3_edge": (image_array([Image(edge[k], dst_e[k], coef[k]) for k in range(n)]),
+                                    n * 3 * (H // 8) * ((W2 + 7) // 8)),
+    }
+    steps = max(1, min(args.steps, 50))
+    rows = {}
+    for name, (arr, blocks) in forms.items():
+        def step(i, arr=arr):
+            st = lib.adct_roundtrip(ctx, arr, n, ctypes.byref(q), sh)
+            if st != 0:
+                raise RuntimeError(lib.adct_last_error(ctx).decode())
+        for i in range(max(3, args.warmup)):
+            step(i)
+        torch.cuda.synchronize()
+        codec.kernel_time()
+        codec.kernel_timing(True)
+        d.barrier()
+        t = d.max(_event_time(step, steps, stream))
+        codec.kernel_timing(False)
+        kms, launches = codec.kernel_time()
+        ks = kms / max(1, launches) / 1000.0
+        rows[name] = {"blocks_s": d.sum(blocks * steps) / t, "kernel_us": 1e6 * ks,
+                      "gbs": blocks * BYTES_PER_BLOCK / ks / 1e9, "frac": blocks * BYTES_PER_BLOCK / ks / 1e9 / peak}
+    torch.cuda.synchronize()
+    same = bool(torch.equal(dst_i, dst_p.permute(0, 2, 3, 1)))
+    head = rows["interleaved_1080x1920x3"]
+    if d.rank == 0:
+        line = {"metric": METRIC, "value": head["blocks_s"], "unit": "blocks/s", "n_gpus": d.ws, "steps": steps,
+                "warmup": max(3, args.warmup), "ms_per_step": n * 3 * (H // 8) * (W // 8) / head["blocks_s"] * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+                "data": "synthetic",
+                "config": {"workload": f"{n} RGB {H}x{W} u8 round trip, step s=4: interleaved HWC (headline) vs "
+                                       f"planar, and planar {H}x{W2} with edge blocks", "l2": "inputs larger than L2"},
+                "roofline": {"bound": "hbm", "achieved": head["gbs"], "peak": peak, "unit": "GB/s",
+                             "frac": head["frac"], "peak_kind": peak_kind, "kernel": "k_codec<RT_FULL, NCH=3>",
+                             "traffic": None},
+                "forms": rows, "interleaved_equals_planar": same}
+        print(json.dumps(line), flush=True)
+    codec.close()
+    d.close()
+    return 0
+
+
 def _event_time(fn, steps, stream):
     import torch
     e0 = torch.cuda.Event(enable_timing=True)
@@ -807,7 +883,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     return {"roundtrip": run_roundtrip, "ragged": run_ragged, "float": run_float,
-            "serving": run_serving, "quality": run_quality, "packed": run_packed}[args.workload](args)
+            "serving": run_serving, "quality": run_quality, "packed": run_packed,
+            "layout": run_layout}[args.workload](args)
 
 
 if __name__ == "__main__":

@@ -78,7 +78,9 @@ enum { ADCT_LAYOUT_PLANAR = 0, ADCT_LAYOUT_INTERLEAVED = 1 };
  *          (HWC: pixel (y, x), channel c at y * pitch + x * channels + c), rows
  *          `pitch` bytes apart (pitch >= width * channels); plane_stride unused.
  * src and dst share the layout, pitch and plane_stride; pitch and plane_stride
- * are multiples of 8.
+ * are multiples of 8, and every row of a plane or image, the last one
+ * included, spans `pitch` addressable bytes (the kernels read whole 8-byte
+ * chunks up to ceil8(width * channels), never beyond pitch).
  *   src   pixels read by the forward transform            (8-byte aligned)
  *   dst   reconstructed pixels (may equal src)            (8-byte aligned)
  *   coef  int16 coefficients, planar and block-major for both pixel layouts:

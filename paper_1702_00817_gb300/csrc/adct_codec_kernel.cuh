@@ -225,6 +225,9 @@ __device__ __forceinline__ uint32_t block_step(uint8_t* __restrict__ in, uint8_t
   constexpr int kZoneN = zone_count(ZS);
   if (pos.plane < 0) return 0;
   const PlaneDesc* d = planes + pos.plane;
+  // valid columns / rows (edge blocks: the rest replicates the last valid one;
+  // the input stage already holds the last valid row in place of the others)
+  const int vc = EDGE ? valid_cols(d, pos) : 8, vr = EDGE ? valid_rows(d, pos) : 8;
   int32_t v[64];
   if (KT::in_pix && NCH == 1) {
     const uint2* st = (const uint2*)in;
@@ -236,6 +239,10 @@ __device__ __forceinline__ uint32_t block_step(uint8_t* __restrict__ in, uint8_t
         v[8 * i + j] = (int32_t)__byte_perm(w.x, 0u, 0x4440 | j);
         v[8 * i + 4 + j] = (int32_t)__byte_perm(w.y, 0u, 0x4440 | j);
       }
+      if (EDGE) {
+#pragma unroll
+        for (int j = 1; j < 8; ++j) v[8 * i + j] = j < vc ? v[8 * i + j] : v[8 * i + j - 1];
+      }
     }
     fwd2d(v);  // Z + 8192 e0 e0^T (raw pixels; the level shift lives in the constants)
   } else if (KT::in_pix) {
@@ -243,7 +250,7 @@ __device__ __forceinline__ uint32_t block_step(uint8_t* __restrict__ in, uint8_t
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) v[8 * i + j] = px[i * 256 * NCH + NCH * j];
+      for (int j = 0; j < 8; ++j) v[8 * i + j] = px[i * 256 * NCH + NCH * (EDGE ? min(j, vc - 1) : j)];
     fwd2d(v);
   } else if (QMODE == QM_ZONAL_ZZ) {
     // packed input: the first r zig-zag coefficients of this block
@@ -343,7 +350,6 @@ __device__ __forceinline__ uint32_t block_step(uint8_t* __restrict__ in, uint8_t
   uint32_t err = 0;
   if (KT::inv) {
     inv2d(v);
-    const int vc = EDGE ? valid_cols(d, pos) : 8, vr = EDGE ? valid_rows(d, pos) : 8;
     if (KT::sse && NCH == 1) {
       // squared error against the input rows, still in the input stage
       const uint2* st = (const uint2*)in;
@@ -546,33 +552,26 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
   // Issue the asynchronous input copies of one tile into stage st (lanes past
   // the end of the chunk copy nothing; the group is committed regardless).
   // Pixels: lane l's 8 NCH bytes of row i go to (i * 32 + l) * 8 NCH, so the
-  // warp's copies of one row cover 256 NCH contiguous bytes.  A block on the
-  // right or bottom edge of an image whose side is not a multiple of 8 is
-  // filled synchronously instead, replicating the last valid column and row.
+  // warp's copies of one row cover 256 NCH contiguous bytes.
   auto issue = [&](int st, const Pos& q) {
-    uint8_t* sp = wsm + st * SP::in_stage;
-    const uint32_t sa = smem_addr(sp);
+    const uint32_t sa = smem_addr(wsm + st * SP::in_stage);
     if (KT::in_pix) {
       if (q.plane >= 0) {
         const PlaneDesc* d = planes + q.plane;
         const int64_t pitch = __ldg(&d->pitch);
         const uint8_t* src = src_of(d) + (int64_t)(8 * q.by) * pitch + 8 * NCH * q.bx;
+        // Edge blocks copy the last valid row in place of the missing ones and
+        // only the 8-byte chunks that hold valid pixels (they end at or
+        // before ceil8(width * NCH) <= pitch, inside the row); the missing
+        // columns are filled from the last valid one when the block is read.
         const int vc = EDGE ? valid_cols(d, q) : 8, vr = EDGE ? valid_rows(d, q) : 8;
-        if (vc == 8 && vr == 8) {
+        const int nchunk = EDGE ? (NCH * vc + 7) / 8 : NCH;
 #pragma unroll
-          for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 8; ++i) {
+          const uint8_t* row = src + (int64_t)(EDGE ? min(i, vr - 1) : i) * pitch;
 #pragma unroll
-            for (int k = 0; k < NCH; ++k) cp_async8(sa + ((i * 32 + lane) * NCH + k) * 8, src + i * pitch + 8 * k);
-        } else {
-          for (int i = 0; i < 8; ++i) {
-            const uint8_t* row = src + (int64_t)min(i, vr - 1) * pitch;
-            uint8_t* dst = sp + (i * 32 + lane) * 8 * NCH;
-            for (int j = 0; j < 8; ++j) {
-              const int x = min(j, vc - 1);
-#pragma unroll
-              for (int k = 0; k < NCH; ++k) dst[NCH * j + k] = row[NCH * x + k];
-            }
-          }
+          for (int k = 0; k < NCH; ++k)
+            if (!EDGE || k < nchunk) cp_async8(sa + ((i * 32 + lane) * NCH + k) * 8, row + 8 * k);
         }
       }
     } else if (QMODE != QM_ZONAL_ZZ && NCH == 1) {
