@@ -197,11 +197,16 @@ def measured_peaks():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the codec kernel's code (line comments and blank lines left out,
+    so that editing a comment keeps recorded counters valid)."""
     h = hashlib.sha256()
     for f in ("adct_codec_kernel.cuh", "adct_codec.cu", "adct_device.cuh", "adct_codec_zonal_lo.cu",
               "adct_codec_zonal_hi.cu"):
-        with open(os.path.join(ROOT, "paper_1702_00817_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1702_00817_gb300", "csrc", f), encoding="utf-8") as fh:
+            for line in fh:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

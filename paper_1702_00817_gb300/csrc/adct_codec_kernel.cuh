@@ -1,26 +1,32 @@
-// Integer codec kernel for sm_103a (templates; instantiated by adct_codec.cu
-// and, specialised on the zonal zone, by adct_codec_zonal_*.cu): the blockwise
-// 2D 14-addition transform
-// (Sec. 2 fast algorithm T = P A3 A2 A1; Sec. 3 8x8 blocks), the D^2-merged
-// quantiser and the inverse, as one persistent kernel over a flattened block
-// index.  The path is add-only and bound by HBM bytes, so no tensor cores.
+// Integer codec kernel for sm_103a (templates, instantiated by adct_codec.cu
+// for every kind and quantiser mode, by adct_codec_zonal_*.cu specialised on
+// the zonal zone, by adct_codec_edge.cu for planar images with edge blocks and
+// by adct_codec_interleaved.cu for HWC images): the blockwise 2D 14-addition
+// transform (Sec. 2 fast algorithm T = P A3 A2 A1; Sec. 3 8x8 blocks), the
+// D^2-merged quantiser and the inverse, as one persistent kernel over a
+// flattened block index.  The path is add-only and bound by HBM bytes, so no
+// tensor cores.
 //
 // Work split.  The grid is sized to the SMs; each warp owns a contiguous
-// chunk of the flat block index and walks it in tiles of 32 blocks, one 8x8
-// block per lane.  An 8x8 block lives in 64 registers, so both passes of the
-// separable transform and the transpose between them are register renaming.
+// chunk of the flat block index and walks it in tiles of 32 blocks (32 pixel
+// positions of C channels for interleaved images), one 8x8 block per lane.  An
+// 8x8 block lives in 64 registers, so both passes of the separable transform
+// and the transpose between them are register renaming.
 //
 // Memory pipeline per warp (all in the warp's slice of shared memory):
 //   - the next tile's input is prefetched with cp.async while the current one
-//     is computed (pixels: each lane copies its block's 8 rows, 8 bytes each,
-//     so one copy instruction of the warp moves 256 contiguous bytes;
-//     coefficients: the warp copies the tile's contiguous 4 KB, 512 bytes per
-//     instruction, into a 16-byte-chunk XOR swizzle);
+//     is computed (pixels: each lane copies its block's 8 rows, 8 bytes each
+//     -- 8 C bytes for interleaved images -- so one copy instruction of the
+//     warp moves 256 contiguous bytes; coefficients: the warp copies the
+//     tile's contiguous 4 KB, 512 bytes per instruction, into a 16-byte-chunk
+//     XOR swizzle);
 //   - quantised coefficients of a full tile are staged in the same swizzle and
 //     written back as 512-byte contiguous warp stores (one L2 request per
-//     128-byte line instead of one per 16 bytes);
+//     128-byte line instead of one per 16 bytes); packed zonal coefficients
+//     are staged per lane and written back as one contiguous range;
 //   - reconstructed pixels are stored directly (256 contiguous bytes per warp
-//     instruction already).
+//     instruction already), or, for interleaved images, written back into the
+//     input stage and stored by the warp once every channel is done.
 //
 // Arithmetic per block (one lane):
 //   forward  raw bytes -> 8 row butterflies -> 8 column butterflies (Z + 8192 e0e0^T);
