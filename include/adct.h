@@ -9,12 +9,14 @@
  *          D^2 = diag(2^-a_i), a = (3,1,2,1,3,1,2,1), and C^ = D T is orthogonal (Sec. 2);
  *   fast algorithm  T = P A3 A2 A1: 14 additions per 8-point transform (Sec. 2, Table 1).
  * The image codec follows the paper's JPEG-style experiment (Sec. 3): every 8x8
- * block of a uint8 plane goes through the separable 2D transform, then a
- * quantiser, then the inverse procedure:
+ * block of a uint8 plane (each channel of a planar or interleaved image, edge
+ * blocks extended by replication) goes through the separable 2D transform,
+ * then a quantiser, then the inverse procedure:
  *   forward      Z = T (X - 128) T^T                       rows, then columns, integers
  *   quantise     STEP : q = sgn(Z) floor((2|Z| + Q) / (2Q))  (round half away from zero)
  *                ZONAL: q = Z if zig-zag rank(i,j) < r, else 0   (Sec. 3)
- *                STEP_ZONAL: STEP, then the ZONAL mask; NONE: q = Z
+ *                STEP_ZONAL: STEP, then the ZONAL mask; NONE: q = Z;
+ *                ZONAL_ZZ: ZONAL, storing only the r kept values in zig-zag order
  *   dequantise   S_ij = q_ij Q_ij 2^(6 - a_i - a_j)           (D^2 merged into the step, Sec. 2)
  *   inverse      R = T^T S T                                (T^-1 = T^T D^2, Sec. 2)
  *   reconstruct  pixel = clamp(floor((R + 32) / 64) + 128, 0, 255)

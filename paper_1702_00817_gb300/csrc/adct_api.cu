@@ -1,7 +1,9 @@
 // C ABI of the codec (include/adct.h): argument validation, per-call
-// descriptor tables, the workspace ring, the CUDA-graph cache, the
-// autotuner and the host-buffer pipeline.  Kernels live in adct_codec.cu and
-// adct_float.cu; this file only prepares their parameters and launches them.
+// descriptor tables (one launch per pixel layout class), the workspace ring,
+// the CUDA-graph cache, the autotuner, the host-buffer pipeline, the
+// allocation-free entry point and the multi-GPU sharding plan.  Kernels live
+// in adct_codec*.cu, adct_float.cu and adct_quality.cu; this file only
+// prepares their parameters and launches them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -299,6 +301,13 @@ struct Tables {
   }
 };
 
+// Per-thread table storage, reused call after call so that a steady stream of
+// calls (the serving loop) allocates no host memory for its descriptors.
+Tables& scratch_tables() {
+  static thread_local Tables t;
+  return t;
+}
+
 // Validates the images and builds the descriptor tables of every group.
 adct_status build_tables(adct_context* ctx, const adct_image* imgs, int32_t n, int need, bool coef_only, int32_t cpb,
                          Tables& t) {
@@ -457,7 +466,7 @@ adct_status run_codec(adct_context* ctx, const adct_image* imgs, int32_t n, cons
   if (packed && kind == K_QUANTISE)
     return fail(ctx, ADCT_ERR_UNSUPPORTED, "the packed zonal layout is written by adct_roundtrip, not adct_quantise");
   if (packed && kind == K_INVERSE) cl.qmode = QM_ZONAL_ZZ;
-  Tables t;
+  Tables& t = scratch_tables();
   st = build_tables(ctx, imgs, n, need_for_kind(kind), kind == K_QUANTISE, packed ? quant->r : 64, t);
   if (st != ADCT_OK) return st;
   if (t.blocks == 0) return ADCT_OK;
@@ -699,7 +708,7 @@ adct_status adct_quality_dct(adct_context* ctx, const adct_image* imgs, int32_t 
   for (int32_t m = 0; m < n && imgs; ++m)
     if (imgs[m].layout != ADCT_LAYOUT_PLANAR || imgs[m].width % 8 || imgs[m].height % 8)
       return fail(ctx, ADCT_ERR_UNSUPPORTED, "the DCT comparator takes planar images with sides multiple of 8");
-  Tables t;
+  Tables& t = scratch_tables();
   adct_status st = build_tables(ctx, imgs, n, NEED_SRC, false, 64, t);
   if (st != ADCT_OK) return st;
   if (t.blocks == 0) return ADCT_OK;
@@ -786,7 +795,7 @@ adct_status adct_roundtrip_graph(adct_context* ctx, const adct_image* imgs, int3
   st = build_quant(ctx, quant, true, cl.qp, cl.evenq);
   if (st != ADCT_OK) return st;
   cl.qmode = quant->mode;
-  Tables t;
+  Tables& t = scratch_tables();
   st = build_tables(ctx, imgs, n, need_for_kind(kind), false, coef_per_block(quant), t);
   if (st != ADCT_OK) return st;
   if (t.blocks == 0) return ADCT_OK;
