@@ -324,7 +324,7 @@ def run_roundtrip(args):
     d = Dist()
     dev = torch.device("cuda", d.local)
     torch.cuda.set_device(dev)
-    if d.rank == 0 or not _build.up_to_date():
+    if d.rank == 0:  # one build per node: the other ranks wait, then load it
         _build.build()
     d.barrier()
     n = args.images
@@ -437,7 +437,7 @@ def run_packed(args):
     d = Dist()
     dev = torch.device("cuda", d.local)
     torch.cuda.set_device(dev)
-    if d.rank == 0 or not _build.up_to_date():
+    if d.rank == 0:  # one build per node: the other ranks wait, then load it
         _build.build()
     d.barrier()
     n = args.images
@@ -533,7 +533,7 @@ def run_layout(args):
     d = Dist()
     dev = torch.device("cuda", d.local)
     torch.cuda.set_device(dev)
-    if d.rank == 0 or not _build.up_to_date():
+    if d.rank == 0:  # one build per node: the other ranks wait, then load it
         _build.build()
     d.barrier()
     n, H, W = 64, 1080, 1920
@@ -621,7 +621,7 @@ def run_ragged(args):
     d = Dist()
     dev = torch.device("cuda", d.local)
     torch.cuda.set_device(dev)
-    if d.rank == 0 or not _build.up_to_date():
+    if d.rank == 0:  # one build per node: the other ranks wait, then load it
         _build.build()
     d.barrier()
     # one ragged batch of 1000 images per GPU, sharded over the ranks by the
@@ -710,7 +710,7 @@ def run_float(args):
     d = Dist()
     dev = torch.device("cuda", d.local)
     torch.cuda.set_device(dev)
-    if d.rank == 0 or not _build.up_to_date():
+    if d.rank == 0:  # one build per node: the other ranks wait, then load it
         _build.build()
     d.barrier()
     x = torch.from_numpy(inputs.normal_batch((64, 3, 512, 512), seed=inputs.BASE_SEED + d.rank)).to(dev)
@@ -769,7 +769,7 @@ def run_serving(args):
     d = Dist()
     dev = torch.device("cuda", d.local)
     torch.cuda.set_device(dev)
-    if d.rank == 0 or not _build.up_to_date():
+    if d.rank == 0:  # one build per node: the other ranks wait, then load it
         _build.build()
     d.barrier()
     sizes = [(256, 256), (512, 512), (1080, 1920), (2160, 3840), (4096, 4096)]
@@ -836,7 +836,7 @@ def run_quality(args):
     d = Dist()
     dev = torch.device("cuda", d.local)
     torch.cuda.set_device(dev)
-    if d.rank == 0 or not _build.up_to_date():
+    if d.rank == 0:  # one build per node: the other ranks wait, then load it
         _build.build()
     d.barrier()
     n, side = 45, 512
