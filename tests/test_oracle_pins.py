@@ -277,6 +277,27 @@ def test_float_adjoint_matches_central_finite_differences(Qkind):
         assert abs(fd - an) <= 1e-4 * max(1.0, abs(an))
 
 
+def test_float_adjoint_passes_torch_gradcheck():
+    """The whole Jacobian of a 1x16x16 input, in float64, by torch's own
+    numerical differentiation, against the oracle's analytic adjoint."""
+    import torch
+    Q = inputs.step_table(1).astype(np.float64)
+
+    class Fp64(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, x):
+            ctx.save_for_backward(x)
+            return torch.from_numpy(oracle.forward_f64(x.detach().numpy(), Q))
+
+        @staticmethod
+        def backward(ctx, g):
+            (x,) = ctx.saved_tensors
+            return torch.from_numpy(oracle.backward_f64(x.numpy(), g.contiguous().numpy(), Q))
+
+    x = torch.from_numpy(np.random.default_rng(5).standard_normal((1, 16, 16))).requires_grad_(True)
+    assert torch.autograd.gradcheck(Fp64.apply, (x,), eps=1e-6, atol=1e-6, rtol=1e-5)
+
+
 def test_dct_comparator_is_orthonormal_and_exact_at_r64():
     # the exact DCT of the Sec. 3 comparison: C C^T = I; keeping all 64
     # coefficients reproduces every image exactly (after rounding)
