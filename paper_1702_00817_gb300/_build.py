@@ -64,7 +64,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         raise RuntimeError(f"nvcc failed for {failed}:\n{msgs}")
     tmp = LIB + f".{os.getpid()}.tmp"
     cuda_lib = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")
-    link = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "shared", "-Xlinker", f"-rpath,{cuda_lib}"]
+    link = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "shared", "-ldl", "-Xlinker", f"-rpath,{cuda_lib}"]
     subprocess.check_call(link)
     os.replace(tmp, LIB)
     if verbose:

@@ -5,6 +5,7 @@
 // in adct_codec*.cu, adct_float.cu and adct_quality.cu; this file only
 // prepares their parameters and launches them.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -73,6 +74,13 @@ struct adct_context {
 };
 
 namespace {
+
+// NVTX range around one entry point, visible to Nsight tools (free when no
+// tool is attached).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 struct DeviceGuard {
   int prev = -1;
@@ -666,21 +674,25 @@ adct_status adct_kernel_time(adct_context* ctx, double* total_ms, int64_t* launc
 }
 
 adct_status adct_forward(adct_context* ctx, const adct_image* imgs, int32_t n, adct_stream_t stream) {
+  Range nvtx("adct_forward");
   return run_codec(ctx, imgs, n, nullptr, K_FORWARD, (cudaStream_t)stream, ctx ? ctx->shape : LaunchShape{});
 }
 
 adct_status adct_quantise(adct_context* ctx, const adct_image* imgs, int32_t n, const adct_quant* quant,
                           adct_stream_t stream) {
+  Range nvtx("adct_quantise");
   return run_codec(ctx, imgs, n, quant, K_QUANTISE, (cudaStream_t)stream, ctx ? ctx->shape : LaunchShape{});
 }
 
 adct_status adct_inverse(adct_context* ctx, const adct_image* imgs, int32_t n, const adct_quant* quant,
                          adct_stream_t stream) {
+  Range nvtx("adct_inverse");
   return run_codec(ctx, imgs, n, quant, K_INVERSE, (cudaStream_t)stream, ctx ? ctx->shape : LaunchShape{});
 }
 
 adct_status adct_roundtrip(adct_context* ctx, const adct_image* imgs, int32_t n, const adct_quant* quant,
                            adct_stream_t stream) {
+  Range nvtx("adct_roundtrip");
   if (!ctx) return ADCT_ERR_INVALID_ARG;
   if (n < 0 || (n > 0 && !imgs)) return fail(ctx, ADCT_ERR_INVALID_ARG, "bad image list");
   bool ok = true;
@@ -692,6 +704,7 @@ adct_status adct_roundtrip(adct_context* ctx, const adct_image* imgs, int32_t n,
 
 adct_status adct_quality(adct_context* ctx, const adct_image* imgs, int32_t n, const adct_quant* quant, uint64_t* sse,
                          adct_stream_t stream) {
+  Range nvtx("adct_quality");
   if (!ctx) return ADCT_ERR_INVALID_ARG;
   if (n > 0 && !sse) return fail(ctx, ADCT_ERR_INVALID_ARG, "sse is NULL");
   if ((uintptr_t)sse % 8) return fail(ctx, ADCT_ERR_ALIGN, "sse must be 8-byte aligned");
@@ -700,6 +713,7 @@ adct_status adct_quality(adct_context* ctx, const adct_image* imgs, int32_t n, c
 
 adct_status adct_quality_dct(adct_context* ctx, const adct_image* imgs, int32_t n, int32_t r, uint64_t* sse,
                              adct_stream_t stream) {
+  Range nvtx("adct_quality_dct");
   if (!ctx) return ADCT_ERR_INVALID_ARG;
   ctx->last_error.clear();
   if (r < 0 || r > 64) return fail(ctx, ADCT_ERR_INVALID_ARG, "r outside 0..64");
@@ -752,6 +766,7 @@ adct_status adct_quality_dct(adct_context* ctx, const adct_image* imgs, int32_t 
 
 adct_status adct_forward_f32(adct_context* ctx, const float* x, float* y, int64_t planes, int32_t H, int32_t W,
                              const float* Qsoft, adct_stream_t stream) {
+  Range nvtx("adct_forward_f32");
   adct_status st = check_float(ctx, x, y, y, planes, H, W);
   if (st != ADCT_OK) return st;
   FloatParams fp;
@@ -765,6 +780,7 @@ adct_status adct_forward_f32(adct_context* ctx, const float* x, float* y, int64_
 
 adct_status adct_backward_f32(adct_context* ctx, const float* x, const float* gy, float* gx, int64_t planes,
                               int32_t H, int32_t W, const float* Qsoft, adct_stream_t stream) {
+  Range nvtx("adct_backward_f32");
   adct_status st = check_float(ctx, x, gy, gx, planes, H, W);
   if (st != ADCT_OK) return st;
   FloatParams fp;
@@ -779,6 +795,7 @@ adct_status adct_backward_f32(adct_context* ctx, const float* x, const float* gy
 
 adct_status adct_roundtrip_graph(adct_context* ctx, const adct_image* imgs, int32_t n, const adct_quant* quant,
                                  adct_stream_t stream, int32_t* replayed) {
+  Range nvtx("adct_roundtrip_graph");
   if (!ctx) return ADCT_ERR_INVALID_ARG;
   ctx->last_error.clear();
   if (replayed) *replayed = 0;
@@ -851,6 +868,7 @@ adct_status adct_roundtrip_graph(adct_context* ctx, const adct_image* imgs, int3
 
 adct_status adct_autotune(adct_context* ctx, const adct_image* imgs, int32_t n, const adct_quant* quant,
                           adct_stream_t stream, int32_t reps, adct_launch* best, float* best_us) {
+  Range nvtx("adct_autotune");
   if (!ctx || !best || reps < 1) return ADCT_ERR_INVALID_ARG;
   bool ok = true;
   if (n < 1 || !imgs) return fail(ctx, ADCT_ERR_INVALID_ARG, "autotune needs at least one image");
@@ -901,6 +919,7 @@ done:
 
 adct_status adct_roundtrip_host(adct_context* ctx, const adct_image* himgs, int32_t n, const adct_quant* quant,
                                 int64_t chunk_bytes) {
+  Range nvtx("adct_roundtrip_host");
   if (!ctx) return ADCT_ERR_INVALID_ARG;
   ctx->last_error.clear();
   if (n < 0 || (n > 0 && !himgs)) return fail(ctx, ADCT_ERR_INVALID_ARG, "bad image list");
@@ -1191,6 +1210,7 @@ adct_status noalloc_device(int dev, void** scratch, int* sm_count) {
 
 extern "C" adct_status adct_roundtrip_noalloc(const adct_image* imgs, int32_t n, const adct_quant* quant,
                                               adct_stream_t stream) {
+  Range nvtx("adct_roundtrip_noalloc");
   if (n < 0 || (n > 0 && !imgs) || !quant) return ADCT_ERR_INVALID_ARG;
   if (n == 0) return ADCT_OK;
   const bool want_coef = imgs[0].coef != nullptr, want_dst = imgs[0].dst != nullptr;
