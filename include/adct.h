@@ -270,6 +270,18 @@ adct_status adct_roundtrip_host(adct_context* ctx, const adct_image* host_imgs, 
                                 int64_t chunk_bytes);
 
 /*
+ * Bounds-check report of the checked build (libadct_checked.so, compiled with
+ * ADCT_CHECKED; the paper has no counterpart -- a stand-in for a memory
+ * checker).  Its kernels verify that every tile position lies inside its
+ * plane's blocks and that no pixel copy passes the end of a row; a violation
+ * sets a bit (1: position, 2: row bytes) in a per-context device word and the
+ * access is skipped.  This call waits for the device, returns the word in
+ * *faults and clears it.  The release build returns ADCT_ERR_UNSUPPORTED with
+ * *faults = 0.
+ */
+adct_status adct_checked_faults(adct_context* ctx, uint32_t* faults);
+
+/*
  * Multi-GPU sharding of one batch, with no collective (the blocks of different
  * images never interact, Sec. 3): a deterministic partition of the n images
  * over `world` ranks balanced by 8x8 block count -- images taken largest first

@@ -11,6 +11,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libadct.so")
+LIB_CHECKED = os.path.join(PKG, "libadct_checked.so")  # kernels with bounds checks (ADCT_CHECKED)
 SOURCES = ["adct_api.cu", "adct_codec.cu", "adct_codec_zonal_lo.cu", "adct_codec_zonal_hi.cu",
            "adct_codec_interleaved.cu", "adct_codec_edge.cu", "adct_float.cu", "adct_quality.cu", "adct_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -31,27 +32,33 @@ def _inputs():
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(checked: bool = False) -> bool:
+    lib = LIB_CHECKED if checked else LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every CUDA source for sm_103a and link libadct.so next to this file."""
-    if not force and up_to_date():
-        return LIB
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile every CUDA source for sm_103a and link libadct.so next to this
+    file (checked: libadct_checked.so, whose kernels check their bounds)."""
+    LIB_OUT = LIB_CHECKED if checked else LIB
+    if not force and up_to_date(checked):
+        return LIB_OUT
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    BUILD_DIR = os.path.join(BUILD, "checked") if checked else BUILD
+    os.makedirs(BUILD_DIR, exist_ok=True)
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    if checked:
+        common += ["-DADCT_CHECKED"]
     procs = []
     objs = []
     for s in SOURCES:
-        obj = os.path.join(BUILD, s.replace(".cu", ".o"))
+        obj = os.path.join(BUILD_DIR, s.replace(".cu", ".o"))
         objs.append(obj)
         cmd = [nvcc] + common + ["-Xptxas", "-v", "-c", os.path.join(CSRC, s), "-o", obj]
-        log = open(os.path.join(BUILD, s + ".log"), "w")
+        log = open(os.path.join(BUILD_DIR, s + ".log"), "w")
         procs.append((subprocess.Popen(cmd, stdout=log, stderr=subprocess.STDOUT), log, s))
     failed = []
     for p, log, s in procs:
@@ -60,13 +67,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if rc != 0:
             failed.append(s)
     if failed:
-        msgs = "".join(open(os.path.join(BUILD, s + ".log")).read()[-4000:] for s in failed)
+        msgs = "".join(open(os.path.join(BUILD_DIR, s + ".log")).read()[-4000:] for s in failed)
         raise RuntimeError(f"nvcc failed for {failed}:\n{msgs}")
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = LIB_OUT + f".{os.getpid()}.tmp"
     cuda_lib = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")
     link = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "shared", "-ldl", "-Xlinker", f"-rpath,{cuda_lib}"]
     subprocess.check_call(link)
-    os.replace(tmp, LIB)
+    os.replace(tmp, LIB_OUT)
     if verbose:
-        print("built", LIB)
-    return LIB
+        print("built", LIB_OUT)
+    return LIB_OUT

@@ -32,6 +32,7 @@ EXPORTS = (
     "adct_autotune", "adct_roundtrip_host", "adct_butterfly_host", "adct_kernel_timing", "adct_kernel_time",
     "adct_roundtrip_noalloc", "adct_quality", "adct_quality_dct", "adct_server_create", "adct_server_destroy", "adct_server_encode",
     "adct_server_decode", "adct_server_poll", "adct_server_stats", "adct_server_clock", "adct_shard_plan",
+    "adct_checked_faults",
     "adct_status_string", "adct_last_error",
 )
 
@@ -98,7 +99,18 @@ def load(path: str | None = None) -> ctypes.CDLL:
     global _lib
     if _lib is not None:
         return _lib
-    path = path or _build.LIB
+    _lib = _open(path or _build.LIB)
+    return _lib
+
+
+def load_checked() -> ctypes.CDLL:
+    """Load libadct_checked.so, the build whose kernels check their own bounds
+    (built by paper_1702_00817_gb300._build.build(checked=True)); a separate
+    library instance next to the release one."""
+    return _open(_build.LIB_CHECKED)
+
+
+def _open(path: str) -> ctypes.CDLL:
     if not os.path.exists(path):
         raise RuntimeError(f"{path} is missing: build the CUDA library first (python -c 'import __graft_entry__ as g; g.build()')")
     lib = ctypes.CDLL(path)
@@ -135,6 +147,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "adct_server_stats": ([P, ctypes.POINTER(adct_server_stats_t)], i32),
         "adct_server_clock": ([], ctypes.c_double),
         "adct_shard_plan": ([I, i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i64)], i32),
+        "adct_checked_faults": ([P, ctypes.POINTER(ctypes.c_uint32)], i32),
         "adct_status_string": ([i32], ctypes.c_char_p),
         "adct_last_error": ([P], ctypes.c_char_p),
     }
@@ -142,13 +155,13 @@ def load(path: str | None = None) -> ctypes.CDLL:
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = res
-    _lib = lib
     return lib
 
 
-def check(status: int, ctx=None, what: str = "") -> None:
+def check(status: int, ctx=None, what: str = "", lib=None) -> None:
+    """Raise AdctError for a non-OK status (lib: the library that owns ctx)."""
     if status != ADCT_OK:
-        lib = load()
+        lib = lib if lib is not None else load()
         name = lib.adct_status_string(status).decode()
         msg = lib.adct_last_error(ctx).decode() if ctx else ""
         raise AdctError(status, f"{what}: {name} {msg}".strip())

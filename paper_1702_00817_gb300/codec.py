@@ -143,11 +143,11 @@ def _qsoft(Qsoft):
 class Codec:
     """A library context bound to one CUDA device."""
 
-    def __init__(self, device: int = 0):
-        self.lib = N.load()
+    def __init__(self, device: int = 0, lib=None):
+        self.lib = lib if lib is not None else N.load()
         self.device = int(device)
         h = ctypes.c_void_p()
-        N.check(self.lib.adct_create(ctypes.byref(h), self.device), None, "adct_create")
+        N.check(self.lib.adct_create(ctypes.byref(h), self.device), None, "adct_create", lib=self.lib)
         self.ctx = h
 
     def close(self):
@@ -174,7 +174,7 @@ class Codec:
         if quant is not None:
             args.append(ctypes.byref(quant))
         args.append(_stream_handle(self.device, stream))
-        N.check(getattr(self.lib, name)(*args), self.ctx, name)
+        N.check(getattr(self.lib, name)(*args), self.ctx, name, lib=self.lib)
 
     def forward(self, images, stream=None):
         self._call("adct_forward", images, None, stream)
@@ -193,16 +193,16 @@ class Codec:
         rep = ctypes.c_int32(0)
         st = self.lib.adct_roundtrip_graph(self.ctx, arr, len(images), ctypes.byref(quant),
                                            _stream_handle(self.device, stream), ctypes.byref(rep))
-        N.check(st, self.ctx, "adct_roundtrip_graph")
+        N.check(st, self.ctx, "adct_roundtrip_graph", lib=self.lib)
         return bool(rep.value)
 
     def set_launch(self, threads_per_cta=0, ctas_per_sm=0, stage_coef=1):
         l = N.adct_launch(threads_per_cta, ctas_per_sm, stage_coef, 0)
-        N.check(self.lib.adct_set_launch(self.ctx, ctypes.byref(l)), self.ctx, "adct_set_launch")
+        N.check(self.lib.adct_set_launch(self.ctx, ctypes.byref(l)), self.ctx, "adct_set_launch", lib=self.lib)
 
     def get_launch(self) -> dict:
         l = N.adct_launch()
-        N.check(self.lib.adct_get_launch(self.ctx, ctypes.byref(l)), self.ctx, "adct_get_launch")
+        N.check(self.lib.adct_get_launch(self.ctx, ctypes.byref(l)), self.ctx, "adct_get_launch", lib=self.lib)
         return {f: getattr(l, f) for f, _ in N.adct_launch._fields_}
 
     def autotune(self, images, quant, reps: int = 5, stream=None):
@@ -212,14 +212,14 @@ class Codec:
         st = self.lib.adct_autotune(self.ctx, arr, len(images), ctypes.byref(quant),
                                     _stream_handle(self.device, stream), int(reps), ctypes.byref(best),
                                     ctypes.byref(us))
-        N.check(st, self.ctx, "adct_autotune")
+        N.check(st, self.ctx, "adct_autotune", lib=self.lib)
         return {f: getattr(best, f) for f, _ in N.adct_launch._fields_}, us.value
 
     def roundtrip_host(self, images, quant, chunk_bytes: int = 64 << 20):
         """End-to-end round trip on host (ideally pinned) tensors; synchronous."""
         arr = image_array(images, quant)
         st = self.lib.adct_roundtrip_host(self.ctx, arr, len(images), ctypes.byref(quant), int(chunk_bytes))
-        N.check(st, self.ctx, "adct_roundtrip_host")
+        N.check(st, self.ctx, "adct_roundtrip_host", lib=self.lib)
 
     def quality(self, images, quant, stream=None) -> torch.Tensor:
         """Per-plane sum of squared round-trip error (int64 tensor on the device)."""
@@ -228,7 +228,7 @@ class Codec:
         sse = torch.empty(max(1, planes), dtype=torch.int64, device=torch.device("cuda", self.device))
         st = self.lib.adct_quality(self.ctx, arr, len(images), ctypes.byref(quant), sse.data_ptr(),
                                    _stream_handle(self.device, stream))
-        N.check(st, self.ctx, "adct_quality")
+        N.check(st, self.ctx, "adct_quality", lib=self.lib)
         return sse[:planes]
 
     def quality_dct(self, images, r: int, stream=None) -> torch.Tensor:
@@ -238,17 +238,27 @@ class Codec:
         sse = torch.empty(max(1, planes), dtype=torch.int64, device=torch.device("cuda", self.device))
         st = self.lib.adct_quality_dct(self.ctx, arr, len(images), int(r), sse.data_ptr(),
                                        _stream_handle(self.device, stream))
-        N.check(st, self.ctx, "adct_quality_dct")
+        N.check(st, self.ctx, "adct_quality_dct", lib=self.lib)
         return sse[:planes]
 
+    def checked_faults(self) -> int:
+        """Bounds-check fault bits of a checked-build context (waits for the
+        device, then clears them); AdctError(UNSUPPORTED) on the release build."""
+        w = ctypes.c_uint32(0)
+        N.check(self.lib.adct_checked_faults(self.ctx, ctypes.byref(w)), self.ctx, "adct_checked_faults",
+                lib=self.lib)
+        return w.value
+
     def kernel_timing(self, enable: bool):
-        N.check(self.lib.adct_kernel_timing(self.ctx, 1 if enable else 0), self.ctx, "adct_kernel_timing")
+        N.check(self.lib.adct_kernel_timing(self.ctx, 1 if enable else 0), self.ctx, "adct_kernel_timing",
+                lib=self.lib)
 
     def kernel_time(self):
         """(summed kernel ms, kernels launched) since the previous query."""
         ms = ctypes.c_double(0)
         n = ctypes.c_int64(0)
-        N.check(self.lib.adct_kernel_time(self.ctx, ctypes.byref(ms), ctypes.byref(n)), self.ctx, "adct_kernel_time")
+        N.check(self.lib.adct_kernel_time(self.ctx, ctypes.byref(ms), ctypes.byref(n)), self.ctx, "adct_kernel_time",
+                lib=self.lib)
         return ms.value, n.value
 
     # -- float variant ------------------------------------------------------
@@ -258,7 +268,7 @@ class Codec:
         _f32(y, "out")
         st = self.lib.adct_forward_f32(self.ctx, x.data_ptr(), y.data_ptr(), planes, H, W, _qsoft(Qsoft),
                                        _stream_handle(self.device, stream))
-        N.check(st, self.ctx, "adct_forward_f32")
+        N.check(st, self.ctx, "adct_forward_f32", lib=self.lib)
         return y
 
     def backward_f32(self, x: torch.Tensor, gy: torch.Tensor, Qsoft=None, out: torch.Tensor | None = None,
@@ -268,7 +278,7 @@ class Codec:
         gx = torch.empty_like(x) if out is None else out
         st = self.lib.adct_backward_f32(self.ctx, x.data_ptr(), gy.data_ptr(), gx.data_ptr(), planes, H, W,
                                         _qsoft(Qsoft), _stream_handle(self.device, stream))
-        N.check(st, self.ctx, "adct_backward_f32")
+        N.check(st, self.ctx, "adct_backward_f32", lib=self.lib)
         return gx
 
 

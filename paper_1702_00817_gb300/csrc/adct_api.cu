@@ -71,6 +71,7 @@ struct adct_context {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> tev;
   size_t tev_used = 0;
   int64_t launches = 0;
+  unsigned int* fault = nullptr;  // device word for the bounds checks of a checked build
 };
 
 namespace {
@@ -465,6 +466,7 @@ adct_status run_codec(adct_context* ctx, const adct_image* imgs, int32_t n, cons
   CodecLaunch cl{};
   cl.kind = kind;
   cl.qmode = QM_NONE;
+  cl.fault = ctx->fault;
   if (kind != K_FORWARD && !quant) return fail(ctx, ADCT_ERR_INVALID_ARG, "quant is NULL");
   const bool pixel_input = (kind != K_QUANTISE && kind != K_INVERSE);
   st = build_quant(ctx, kind == K_FORWARD ? nullptr : quant, pixel_input, cl.qp, cl.evenq);
@@ -586,6 +588,12 @@ adct_status adct_create(adct_context** out, int32_t device) {
     adct_destroy(ctx);
     return ADCT_ERR_CUDA;
   }
+  if (cudaMalloc(&ctx->fault, sizeof(unsigned int)) != cudaSuccess ||
+      cudaMemset(ctx->fault, 0, sizeof(unsigned int)) != cudaSuccess) {
+    cudaGetLastError();
+    adct_destroy(ctx);
+    return ADCT_ERR_OOM;
+  }
   *out = ctx;
   return ADCT_OK;
 }
@@ -593,6 +601,10 @@ adct_status adct_create(adct_context** out, int32_t device) {
 void adct_destroy(adct_context* ctx) {
   if (!ctx) return;
   DeviceGuard guard(ctx->device);
+  if (ctx->fault) {
+    cudaDeviceSynchronize();
+    cudaFree(ctx->fault);
+  }
   for (auto& s : ctx->slots) {
     if (s.done) {
       if (s.pending) cudaEventSynchronize(s.done);
@@ -654,6 +666,22 @@ adct_status adct_kernel_timing(adct_context* ctx, int32_t enable) {
   if (!ctx) return ADCT_ERR_INVALID_ARG;
   ctx->timing = enable != 0;
   return ADCT_OK;
+}
+
+adct_status adct_checked_faults(adct_context* ctx, uint32_t* faults) {
+  if (!ctx || !faults) return ADCT_ERR_INVALID_ARG;
+  *faults = 0;
+#ifdef ADCT_CHECKED
+  DeviceGuard guard(ctx->device);
+  ADCT_CUDA(ctx, cudaDeviceSynchronize());
+  unsigned int w = 0;
+  ADCT_CUDA(ctx, cudaMemcpy(&w, ctx->fault, sizeof w, cudaMemcpyDeviceToHost));
+  ADCT_CUDA(ctx, cudaMemset(ctx->fault, 0, sizeof w));
+  *faults = w;
+  return ADCT_OK;
+#else
+  return fail(ctx, ADCT_ERR_UNSUPPORTED, "bounds checks exist in the checked build only (libadct_checked.so)");
+#endif
 }
 
 adct_status adct_kernel_time(adct_context* ctx, double* total_ms, int64_t* launches) {
@@ -808,6 +836,7 @@ adct_status adct_roundtrip_graph(adct_context* ctx, const adct_image* imgs, int3
   if (st != ADCT_OK) return st;
   CodecLaunch cl{};
   cl.kind = kind;
+  cl.fault = ctx->fault;
   if (!quant) return fail(ctx, ADCT_ERR_INVALID_ARG, "quant is NULL");
   st = build_quant(ctx, quant, true, cl.qp, cl.evenq);
   if (st != ADCT_OK) return st;

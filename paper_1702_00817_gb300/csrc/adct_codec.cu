@@ -118,7 +118,7 @@ cudaError_t launch_codec(const CodecLaunch& c, const LaunchShape& shape, int sm_
   int64_t chunk = (c.total + warps - 1) / warps;
   chunk = (chunk + kTile - 1) / kTile * kTile;
   fn<<<grid, shape.threads, smem, stream>>>(c.planes, c.starts, c.nplanes, c.total, chunk, shape.stage_coef, c.sse,
-                                            c.qp);
+                                            c.fault, c.qp);
   return cudaGetLastError();
 }
 

@@ -526,7 +526,8 @@ __device__ __forceinline__ void write_back_zz(const uint8_t* __restrict__ stage_
 template <int KIND, int QMODE, bool EVENQ, int ZS, int NCH = 1, bool EDGE = false>
 __global__ void __launch_bounds__(kMaxThreads, 3)
 k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts, int32_t nplanes, int64_t total,
-        int64_t chunk, int stage_coef, unsigned long long* __restrict__ sse, const QuantParams qp) {
+        int64_t chunk, int stage_coef, unsigned long long* __restrict__ sse, unsigned int* __restrict__ fault,
+        const QuantParams qp) {
   using KT = KindTraits<KIND>;
   using SP = SmemPlan<KIND, NCH>;
   constexpr int S = SP::stages;
@@ -555,6 +556,20 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
     cur.last.by = cur.last.bx = 0;
   }
 
+  // Checked builds (ADCT_CHECKED): a position outside its plane's blocks is
+  // reported in the fault word and dropped (every address of a block derives
+  // from its plane descriptor and (by, bx)); release builds return it as is.
+  auto checked = [&](Pos q) {
+#ifdef ADCT_CHECKED
+    if (q.plane >= 0 && (q.plane >= nplanes || q.by >= (uint32_t)__ldg(&planes[q.plane].hb) ||
+                         q.bx >= (uint32_t)__ldg(&planes[q.plane].wb))) {
+      if (fault) atomicOr(fault, FAULT_POSITION);
+      q.plane = -1;
+    }
+#endif
+    return q;
+  };
+
   // Issue the asynchronous input copies of one tile into stage st (lanes past
   // the end of the chunk copy nothing; the group is committed regardless).
   // Pixels: lane l's 8 NCH bytes of row i go to (i * 32 + l) * 8 NCH, so the
@@ -572,6 +587,13 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
         // columns are filled from the last valid one when the block is read.
         const int vc = EDGE ? valid_cols(d, q) : 8, vr = EDGE ? valid_rows(d, q) : 8;
         const int nchunk = EDGE ? (NCH * vc + 7) / 8 : NCH;
+#ifdef ADCT_CHECKED
+        if (8 * NCH * (int64_t)q.bx + 8 * nchunk > pitch) {  // a copy would pass the end of the row
+          if (fault) atomicOr(fault, FAULT_ROW_BYTES);
+          cp_async_commit();
+          return;
+        }
+#endif
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const uint8_t* row = src + (int64_t)(EDGE ? min(i, vr - 1) : i) * pitch;
@@ -612,13 +634,13 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
   Pos ring[S - 1];  // positions of tiles i .. i + S - 2, whose copies are issued
 #pragma unroll
   for (int k = 0; k < S - 1; ++k) {
-    ring[k] = cur.locate(planes, starts, begin, kTile * k + lane, rend);
+    ring[k] = checked(cur.locate(planes, starts, begin, kTile * k + lane, rend));
     issue(k, ring[k]);
   }
   int s = 0;  // stage of tile i
   for (int32_t base = 0; base < rend; base += kTile) {
     __syncwarp();  // every lane is done reading tile i - 1's stage, refilled now
-    const Pos pl = cur.locate(planes, starts, begin, base + kTile * (S - 1) + lane, rend);
+    const Pos pl = checked(cur.locate(planes, starts, begin, base + kTile * (S - 1) + lane, rend));
     issue(s == 0 ? S - 1 : s - 1, pl);
     cp_async_wait<S - 1>();
     __syncwarp();

@@ -35,6 +35,7 @@ struct CodecLaunch {
   int qmode;                // QMode (quantiser applied by QUANTISE / RT kinds)
   bool evenq;               // the step table has an even step <= 16384 (tie correction needed)
   unsigned long long* sse;  // K_RT_SSE: per-plane sums of squared reconstruction error (device)
+  unsigned int* fault;      // checked builds: bits set by the kernels' bounds checks (device; may be NULL)
   int nch;                  // 1: planar planes; 3 or 4: interleaved images
   bool edge;                // some image has a side that is not a multiple of 8
   QuantParams qp;
@@ -42,7 +43,11 @@ struct CodecLaunch {
 
 // One instantiation of the integer codec kernel.
 using KernelFn = void (*)(const PlaneDesc*, const int64_t*, int32_t, int64_t, int64_t, int, unsigned long long*,
-                          const QuantParams);
+                          unsigned int*, const QuantParams);
+
+// Bits of the fault word of a checked build (ADCT_CHECKED): a tile position
+// outside its plane's blocks, a pixel copy past the row pitch.
+enum CheckedFault : unsigned int { FAULT_POSITION = 1u, FAULT_ROW_BYTES = 2u };
 
 // Zonal kernels specialised on the zone (adct_codec_zonal_lo.cu: zones
 // 0..kZoneLoMax; adct_codec_zonal_hi.cu: up to kZoneHiMax); nullptr when the
