@@ -536,7 +536,7 @@ def run_layout(args):
     if d.rank == 0:  # one build per node: the other ranks wait, then load it
         _build.build()
     d.barrier()
-    n, H, W = 64, 1080, 1920
+    n, H, W = (64 if args.images == N_IMG else args.images), 1080, 1920
     codec = Codec(d.local)
     lib, ctx = codec.lib, codec.ctx
     stream = torch.cuda.current_stream(dev)
