@@ -8,6 +8,8 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <atomic>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -73,6 +75,18 @@ struct adct_context {
   int64_t launches = 0;
   unsigned int* fault = nullptr;  // device word for the bounds checks of a checked build
 };
+
+namespace adct {
+cudaError_t device_alloc(void** ptr, size_t bytes) {
+  static const long long fail_at = [] {
+    const char* e = std::getenv("ADCT_FAULT_INJECT");
+    return (e && std::strncmp(e, "alloc:", 6) == 0) ? std::atoll(e + 6) : 0ll;
+  }();
+  static std::atomic<long long> calls{0};
+  if (fail_at > 0 && ++calls == fail_at) return cudaErrorMemoryAllocation;
+  return cudaMalloc(ptr, bytes);
+}
+}  // namespace adct
 
 namespace {
 
@@ -386,7 +400,7 @@ adct_status acquire_slot(adct_context* ctx, size_t bytes, Slot** out) {
     if (s.host) cudaFreeHost(s.host);
     s.dev = s.host = nullptr;
     s.cap = 0;
-    if (cudaMalloc(&s.dev, cap) != cudaSuccess) {
+    if (device_alloc(&s.dev, cap) != cudaSuccess) {
       cudaGetLastError();
       return fail(ctx, ADCT_ERR_OOM, "workspace cudaMalloc failed");
     }
@@ -588,7 +602,7 @@ adct_status adct_create(adct_context** out, int32_t device) {
     adct_destroy(ctx);
     return ADCT_ERR_CUDA;
   }
-  if (cudaMalloc(&ctx->fault, sizeof(unsigned int)) != cudaSuccess ||
+  if (device_alloc((void**)&ctx->fault, sizeof(unsigned int)) != cudaSuccess ||
       cudaMemset(ctx->fault, 0, sizeof(unsigned int)) != cudaSuccess) {
     cudaGetLastError();
     adct_destroy(ctx);
@@ -852,7 +866,7 @@ adct_status adct_roundtrip_graph(adct_context* ctx, const adct_image* imgs, int3
   if (it == ctx->graphs.end()) {
     GraphEntry g;
     g.bytes = bytes;
-    if (cudaMalloc(&g.dev, bytes) != cudaSuccess) {
+    if (device_alloc(&g.dev, bytes) != cudaSuccess) {
       cudaGetLastError();
       return fail(ctx, ADCT_ERR_OOM, "graph workspace cudaMalloc failed");
     }
@@ -1000,7 +1014,8 @@ adct_status adct_roundtrip_host(adct_context* ctx, const adct_image* himgs, int3
       if (p.dst) cudaFree(p.dst);
       p.src = p.dst = nullptr;
       p.pix_cap = 0;
-      if (cudaMalloc(&p.src, pix_cap) != cudaSuccess || cudaMalloc(&p.dst, pix_cap) != cudaSuccess) {
+      if (device_alloc((void**)&p.src, pix_cap) != cudaSuccess ||
+          device_alloc((void**)&p.dst, pix_cap) != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, ADCT_ERR_OOM, "pipeline staging cudaMalloc failed");
       }
@@ -1015,7 +1030,7 @@ adct_status adct_roundtrip_host(adct_context* ctx, const adct_image* himgs, int3
       if (p.coef) cudaFree(p.coef);
       p.coef = nullptr;
       p.coef_cap = 0;
-      if (cudaMalloc(&p.coef, coef_cap) != cudaSuccess) {
+      if (device_alloc((void**)&p.coef, coef_cap) != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, ADCT_ERR_OOM, "pipeline staging cudaMalloc failed");
       }

@@ -60,6 +60,12 @@ KernelFn pick_interleaved_kernel(int kind, int qmode, bool evenq, int nch);
 // Kernels for planar images with edge blocks (adct_codec_edge.cu).
 KernelFn pick_edge_kernel(int kind, int qmode, bool evenq);
 
+// Device allocation of the library (cudaMalloc), with failure injection for
+// tests: the environment variable ADCT_FAULT_INJECT=alloc:K makes the K-th
+// call of the process (counted from 1) fail with cudaErrorMemoryAllocation
+// without allocating, as if the device were out of memory.
+cudaError_t device_alloc(void** ptr, size_t bytes);
+
 // Launches the integer codec kernel.  Returns cudaSuccess or the launch error.
 cudaError_t launch_codec(const CodecLaunch& c, const LaunchShape& shape, int sm_count, cudaStream_t stream);
 

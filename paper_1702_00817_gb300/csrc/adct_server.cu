@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "adct.h"
+#include "adct_internal.h"
 
 namespace {
 
@@ -42,7 +43,7 @@ class Arena {
  public:
   bool init(size_t bytes) {
     bytes_ = (bytes + kAlign - 1) / kAlign * kAlign;
-    if (cudaMalloc(&base_, bytes_) != cudaSuccess) {
+    if (adct::device_alloc((void**)&base_, bytes_) != cudaSuccess) {
       cudaGetLastError();
       base_ = nullptr;
       return false;
