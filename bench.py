@@ -382,7 +382,7 @@ def run_roundtrip(args):
         himgs = [Image(hsrc[k], hdst[k], hcoef[k:k + 1]) for k in range(n)]
         harr = image_array(himgs)
         esteps = max(3, min(args.steps, 10))
-        chunk = 64 << 20
+        chunk = 32 << 20
         for i in range(2):
             st = lib.adct_roundtrip_host(ctx, harr, n, ctypes.byref(quants[i % len(quants)]), chunk)
             assert st == 0, lib.adct_last_error(ctx).decode()
@@ -485,12 +485,12 @@ def run_packed(args):
                 hcoef = torch.empty(tuple(coef.shape), dtype=torch.int16).pin_memory()
                 harr = image_array([Image(hsrc[k], hdst[k], hcoef[k:k + 1]) for k in range(n)], q)
                 for _ in range(2):
-                    assert lib.adct_roundtrip_host(ctx, harr, n, ctypes.byref(q), 64 << 20) == 0
+                    assert lib.adct_roundtrip_host(ctx, harr, n, ctypes.byref(q), 32 << 20) == 0
                 esteps = 3
                 d.barrier()
                 t0 = time.perf_counter()
                 for _ in range(esteps):
-                    assert lib.adct_roundtrip_host(ctx, harr, n, ctypes.byref(q), 64 << 20) == 0
+                    assert lib.adct_roundtrip_host(ctx, harr, n, ctypes.byref(q), 32 << 20) == 0
                 et = d.max(time.perf_counter() - t0)
                 row[name]["e2e_blocks_s"] = d.sum(blocks * esteps) / et
                 row[name]["d2h_bytes_per_step"] = n * H * W + hcoef.numel() * 2

@@ -260,7 +260,7 @@ adct_status adct_autotune(adct_context* ctx, const adct_image* imgs, int32_t n, 
 /*
  * End-to-end round trip on HOST buffers: the adct_image pointers (src, dst,
  * coef) are host memory (pinned memory gives full copy bandwidth).  Images are
- * processed in chunks of about chunk_bytes of pixels, each chunk copied to the
+ * processed in chunks of about chunk_bytes of pixels (<= 0: 32 MiB), each chunk copied to the
  * device, transformed with adct_roundtrip and copied back, with chunks
  * pipelined over the context's copy/compute streams.  Device staging is owned
  * by ctx and grows to the largest chunk.  Synchronous: returns when every

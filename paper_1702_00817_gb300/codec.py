@@ -215,7 +215,7 @@ class Codec:
         N.check(st, self.ctx, "adct_autotune", lib=self.lib)
         return {f: getattr(best, f) for f, _ in N.adct_launch._fields_}, us.value
 
-    def roundtrip_host(self, images, quant, chunk_bytes: int = 64 << 20):
+    def roundtrip_host(self, images, quant, chunk_bytes: int = 32 << 20):
         """End-to-end round trip on host (ideally pinned) tensors; synchronous."""
         arr = image_array(images, quant)
         st = self.lib.adct_roundtrip_host(self.ctx, arr, len(images), ctypes.byref(quant), int(chunk_bytes))

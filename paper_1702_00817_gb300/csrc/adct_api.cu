@@ -966,7 +966,7 @@ adct_status adct_roundtrip_host(adct_context* ctx, const adct_image* himgs, int3
   if (!ctx) return ADCT_ERR_INVALID_ARG;
   ctx->last_error.clear();
   if (n < 0 || (n > 0 && !himgs)) return fail(ctx, ADCT_ERR_INVALID_ARG, "bad image list");
-  if (chunk_bytes <= 0) chunk_bytes = 64ll << 20;
+  if (chunk_bytes <= 0) chunk_bytes = 32ll << 20;  // measured best: 16-32 MB
   bool ok = true;
   const int kind = kind_for_roundtrip(himgs, n, ok);
   if (!ok) return fail(ctx, ADCT_ERR_INVALID_ARG, "coef/dst must be set on all images or on none");
