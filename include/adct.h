@@ -57,7 +57,8 @@ typedef enum {
   ADCT_ERR_CUDA = 5,        /* a CUDA call failed; see adct_last_error */
   ADCT_ERR_TIMEOUT = 6,     /* a bounded wait gave up */
   ADCT_ERR_UNSUPPORTED = 7, /* device is not sm_103 / feature not available */
-  ADCT_ERR_TOO_LARGE = 8    /* more planes than adct_roundtrip_noalloc can hold */
+  ADCT_ERR_TOO_LARGE = 8,   /* more planes than adct_roundtrip_noalloc can hold */
+  ADCT_ERR_CANCELLED = 9    /* a server request withdrawn by adct_server_cancel before it ran */
 } adct_status;
 
 /* Quantiser modes (adct_quant.mode). */
@@ -386,9 +387,16 @@ typedef struct {
   double t_submit, t_admit, t_done;
 } adct_completion;
 
+/*
+ * Server counters.  latency_hist[b] counts completed requests whose latency
+ * (t_done - t_submit) fell in [2^b, 2^(b+1)) microseconds (b = 0 also takes
+ * shorter ones, b = 31 longer ones).
+ */
 typedef struct {
   int64_t launches, admitted, evicted, unknown_handle, oversized, errors, store_entries, arena_free_bytes;
   int32_t max_overlap, reserved;
+  int64_t cancelled;
+  int64_t latency_hist[32];
 } adct_server_stats_t;
 
 adct_status adct_server_create(adct_server** srv, int32_t device, const adct_server_config* cfg);
@@ -399,6 +407,13 @@ adct_status adct_server_encode(adct_server* srv, const uint8_t* pixels, int32_t 
 /* Fails at once (ADCT_ERR_INVALID_ARG) for a handle not in the store. */
 adct_status adct_server_decode(adct_server* srv, uint64_t handle, uint8_t* out, int64_t pitch, double t_submit,
                                uint64_t* request_id, int32_t* width, int32_t* height);
+/*
+ * Withdraws a request that has not been admitted yet: it will not run, and its
+ * completion reports ADCT_ERR_CANCELLED (a cancelled decode releases its pin
+ * on the handle).  A request already admitted runs to completion as usual.
+ * ADCT_ERR_INVALID_ARG: no such pending request (unknown, or already complete).
+ */
+adct_status adct_server_cancel(adct_server* srv, uint64_t request_id);
 /* Moves up to max completions into out, waiting up to wait_us for the first; returns the count. */
 int32_t adct_server_poll(adct_server* srv, adct_completion* out, int32_t max, int32_t wait_us);
 adct_status adct_server_stats(adct_server* srv, adct_server_stats_t* stats);

@@ -20,6 +20,7 @@ ADCT_ERR_CUDA = 5
 ADCT_ERR_TIMEOUT = 6
 ADCT_ERR_UNSUPPORTED = 7
 ADCT_ERR_TOO_LARGE = 8
+ADCT_ERR_CANCELLED = 9
 NOALLOC_MAX_PLANES = 1024
 
 ADCT_Q_NONE, ADCT_Q_STEP, ADCT_Q_ZONAL, ADCT_Q_STEP_ZONAL, ADCT_Q_ZONAL_ZZ = 0, 1, 2, 3, 4
@@ -32,7 +33,7 @@ EXPORTS = (
     "adct_autotune", "adct_roundtrip_host", "adct_butterfly_host", "adct_kernel_timing", "adct_kernel_time",
     "adct_roundtrip_noalloc", "adct_quality", "adct_quality_dct", "adct_server_create", "adct_server_destroy", "adct_server_encode",
     "adct_server_decode", "adct_server_poll", "adct_server_stats", "adct_server_clock", "adct_shard_plan",
-    "adct_checked_faults",
+    "adct_checked_faults", "adct_server_cancel",
     "adct_status_string", "adct_last_error",
 )
 
@@ -78,7 +79,8 @@ class adct_completion(ctypes.Structure):
 class adct_server_stats_t(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("launches", "admitted", "evicted", "unknown_handle", "oversized",
                                               "errors", "store_entries", "arena_free_bytes")] + \
-               [("max_overlap", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+               [("max_overlap", ctypes.c_int32), ("reserved", ctypes.c_int32), ("cancelled", ctypes.c_int64),
+                ("latency_hist", ctypes.c_int64 * 32)]
 
 
 class AdctError(RuntimeError):
@@ -148,6 +150,7 @@ def _open(path: str) -> ctypes.CDLL:
         "adct_server_clock": ([], ctypes.c_double),
         "adct_shard_plan": ([I, i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i64)], i32),
         "adct_checked_faults": ([P, ctypes.POINTER(ctypes.c_uint32)], i32),
+        "adct_server_cancel": ([P, ctypes.c_uint64], i32),
         "adct_status_string": ([i32], ctypes.c_char_p),
         "adct_last_error": ([P], ctypes.c_char_p),
     }

@@ -570,6 +570,7 @@ const char* adct_status_string(adct_status s) {
     case ADCT_ERR_TIMEOUT: return "ADCT_ERR_TIMEOUT";
     case ADCT_ERR_UNSUPPORTED: return "ADCT_ERR_UNSUPPORTED";
     case ADCT_ERR_TOO_LARGE: return "ADCT_ERR_TOO_LARGE";
+    case ADCT_ERR_CANCELLED: return "ADCT_ERR_CANCELLED";
   }
   return "ADCT_ERR_UNKNOWN";
 }

@@ -25,6 +25,7 @@
 #include <mutex>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "adct.h"
@@ -152,13 +153,34 @@ struct adct_server {
 
   std::thread thread;
   std::atomic<bool> stop{false};
+  std::unordered_set<uint64_t> pending;    // submitted, not completed (under mu)
+  std::unordered_set<uint64_t> cancelled;  // cancellation asked while in the scheduler's queue (under mu)
   std::atomic<int64_t> s_launches{0}, s_admitted{0}, s_evicted{0}, s_unknown{0}, s_oversized{0}, s_errors{0};
+  std::atomic<int64_t> s_cancelled{0};
+  std::atomic<int64_t> s_hist[32] = {};
   std::atomic<int32_t> s_max_overlap{0};
 };
 
 namespace {
 
-void complete(adct_server* s, const Req& r, int32_t status, double t_done) {
+int latency_bucket(double seconds) {
+  const double us = seconds * 1e6;
+  int b = 0;
+  while (b < 31 && us >= (double)(2ull << b)) ++b;
+  return b;
+}
+
+// Reports a request's completion.  locked: the caller holds s->mu.
+void complete(adct_server* s, const Req& r, int32_t status, double t_done, bool locked = false) {
+  if (locked) {
+    s->pending.erase(r.id);
+    s->cancelled.erase(r.id);
+  } else {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->pending.erase(r.id);
+    s->cancelled.erase(r.id);
+  }
+  ++s->s_hist[latency_bucket(t_done - r.t_submit)];
   adct_completion c{};
   c.request_id = r.id;
   c.status = status;
@@ -240,6 +262,22 @@ void admit(adct_server* s, std::vector<Req>& enc, std::vector<Req>& dec) {
     s->queue.push_back(s->incoming.front());
     s->incoming.pop_front();
   }
+  if (!s->cancelled.empty()) {  // withdraw cancelled requests still in the queue
+    std::deque<Req> keep;
+    for (Req& r : s->queue) {
+      if (!s->cancelled.count(r.id)) {
+        keep.push_back(r);
+        continue;
+      }
+      if (r.kind == KIND_DECODE) {
+        auto it = s->store.find(r.handle);
+        if (it != s->store.end()) --it->second.refs;
+      }
+      ++s->s_cancelled;
+      complete(s, r, ADCT_ERR_CANCELLED, now_s(), true);
+    }
+    s->queue.swap(keep);
+  }
   while (!s->queue.empty() && (int32_t)(enc.size() + dec.size()) < s->max_batch) {
     Req& r = s->queue.front();
     const size_t pix = (size_t)r.width * r.height;
@@ -249,7 +287,7 @@ void admit(adct_server* s, std::vector<Req>& enc, std::vector<Req>& dec) {
         Req gone = r;
         s->queue.pop_front();
         ++s->s_unknown;
-        complete(s, gone, ADCT_ERR_INVALID_ARG, now_s());
+        complete(s, gone, ADCT_ERR_INVALID_ARG, now_s(), true);
         continue;
       }
       if (!it->second.ready) break;  // its encode is still running: keep FIFO order
@@ -260,7 +298,7 @@ void admit(adct_server* s, std::vector<Req>& enc, std::vector<Req>& dec) {
       Req big = r;
       s->queue.pop_front();
       ++s->s_oversized;
-      complete(s, big, ADCT_ERR_OOM, now_s());
+      complete(s, big, ADCT_ERR_OOM, now_s(), true);
       continue;
     }
     size_t off_tmp = s->arena.alloc(pix), off_coef = SIZE_MAX;
@@ -476,6 +514,7 @@ adct_status adct_server_encode(adct_server* s, const uint8_t* pixels, int32_t wi
   {
     std::lock_guard<std::mutex> lk(s->mu);
     r.id = s->next_id++;
+    s->pending.insert(r.id);
     s->incoming.push_back(r);
   }
   *request_id = r.id;
@@ -500,6 +539,7 @@ adct_status adct_server_decode(adct_server* s, uint64_t handle, uint8_t* out, in
     r.height = it->second.height;
     r.pitch = pitch;
     r.id = s->next_id++;
+    s->pending.insert(r.id);
     s->incoming.push_back(r);
   }
   if (width) *width = r.width;
@@ -530,11 +570,34 @@ adct_status adct_server_stats(adct_server* s, adct_server_stats_t* st) {
   st->oversized = s->s_oversized;
   st->errors = s->s_errors;
   st->max_overlap = s->s_max_overlap;
+  st->reserved = 0;
+  st->cancelled = s->s_cancelled;
+  for (int b = 0; b < 32; ++b) st->latency_hist[b] = s->s_hist[b];
   {
     std::lock_guard<std::mutex> lk(s->mu);
     st->store_entries = (int64_t)s->store.size();
     st->arena_free_bytes = (int64_t)s->arena.free_bytes();
   }
+  return ADCT_OK;
+}
+
+adct_status adct_server_cancel(adct_server* s, uint64_t request_id) {
+  if (!s) return ADCT_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (!s->pending.count(request_id)) return ADCT_ERR_INVALID_ARG;
+  for (auto it = s->incoming.begin(); it != s->incoming.end(); ++it) {
+    if (it->id != request_id) continue;
+    const Req r = *it;  // not yet seen by the scheduler: withdraw it here
+    s->incoming.erase(it);
+    if (r.kind == KIND_DECODE) {
+      auto e = s->store.find(r.handle);
+      if (e != s->store.end()) --e->second.refs;
+    }
+    ++s->s_cancelled;
+    complete(s, r, ADCT_ERR_CANCELLED, now_s(), true);
+    return ADCT_OK;
+  }
+  s->cancelled.insert(request_id);  // in the scheduler's queue, or already admitted
   return ADCT_OK;
 }
 

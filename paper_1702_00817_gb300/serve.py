@@ -46,6 +46,7 @@ class Request:
     _need: int = 0
     _pinned: bool = False
     _dev: list = field(default_factory=list)
+    _id: int = 0                    # NativeServer: the library's request id
 
     @property
     def latency(self) -> float:
@@ -122,6 +123,27 @@ class Server:
 
     def decode(self, handle: int) -> Request:
         return self.submit(Request("decode", handle=handle))
+
+    def cancel(self, req: Request) -> bool:
+        """Withdraw a request that has not been admitted yet; it completes with
+        error "ADCT_ERR_CANCELLED".  False when it is already running or done."""
+        with self._lock:
+            for q in (self._arrivals, self._queue):
+                at = next((k for k, x in enumerate(q) if x is req), None)  # by identity
+                if at is not None:
+                    del q[at]
+                    if req._pinned:
+                        e = self.store.get(req.handle)
+                        if e is not None:
+                            e["refs"] -= 1
+                        req._pinned = False
+                    req.error = "ADCT_ERR_CANCELLED"
+                    req.result = None
+                    req.t_done = time.perf_counter()
+                    self.stats["cancelled"] = self.stats.get("cancelled", 0) + 1
+                    req.done.set()
+                    return True
+        return False
 
     def warm_host_buffers(self, shapes, count: int = 8) -> None:
         """Pre-fault pinned output buffers of the given [H, W] shapes so that
@@ -417,6 +439,7 @@ class NativeServer:
                 req.done.set()
                 return req
             self._pending[rid.value] = req
+            req._id = rid.value
         return req
 
     def encode(self, pixels: torch.Tensor) -> Request:
@@ -424,6 +447,11 @@ class NativeServer:
 
     def decode(self, handle: int) -> Request:
         return self.submit(Request("decode", handle=handle))
+
+    def cancel(self, req: Request) -> bool:
+        """Withdraw a request that has not been admitted yet (adct_server_cancel);
+        it completes with error "ADCT_ERR_CANCELLED" if it had not run."""
+        return req._id != 0 and self.lib.adct_server_cancel(self._srv, req._id) == self._N.ADCT_OK
 
     def _poll_loop(self):
         ct, N = self._ct, self._N
@@ -452,7 +480,9 @@ class NativeServer:
     def stats(self) -> dict:
         st = self._N.adct_server_stats_t()
         self.lib.adct_server_stats(self._srv, self._ct.byref(st))
-        return {f: getattr(st, f) for f, _ in st._fields_ if f != "reserved"}
+        out = {f: getattr(st, f) for f, _ in st._fields_ if f not in ("reserved", "latency_hist")}
+        out["latency_hist"] = list(st.latency_hist)
+        return out
 
     def drain(self, timeout: float = 60.0) -> None:
         t_end = time.perf_counter() + timeout

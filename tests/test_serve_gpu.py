@@ -134,3 +134,41 @@ def test_native_clock_is_the_perf_counter_clock():
     tn = lib.adct_server_clock()
     t1 = time.perf_counter()
     assert t0 - 1e-3 <= tn <= t1 + 1e-3
+
+
+@pytest.mark.parametrize("server_cls", [Server, NativeServer])
+def test_cancel_withdraws_queued_requests(images, server_cls):
+    """Requests queued behind a memory-bound backlog can be withdrawn: they
+    complete as cancelled and never run; the others complete normally, every
+    request exactly once, and nothing stays pinned or allocated."""
+    q = make_quant(ADCT_Q_STEP, inputs.step_table(4))
+    big = images[(1080, 1920)][0]
+    srv = server_cls(0, budget_bytes=16 << 20, streams=2, quant=q)  # room for two encodes at a time
+    try:
+        reqs = [srv.encode(big) for _ in range(24)]
+        flags = [srv.cancel(r) for r in reqs[8:]]
+        for r in reqs:
+            assert r.done.wait(60)
+        cancelled = [r for r in reqs if r.error == "ADCT_ERR_CANCELLED"]
+        # the Python scheduler reports exactly what it withdrew; the native one
+        # also accepts a request that was admitted meanwhile (it then runs)
+        assert len(cancelled) == sum(flags) or server_cls is NativeServer
+        assert len(cancelled) >= 1
+        assert all(r.error is None for r in reqs if r.error != "ADCT_ERR_CANCELLED")
+        assert all(r.result is None for r in cancelled)
+        # a finished request cannot be cancelled any more
+        assert not srv.cancel(reqs[0])
+        # a decode of the newest encode that ran (older ones are evicted from
+        # this small store) is still correct
+        _, px_ref = oracle.roundtrip(big.numpy(), oracle.MODE_STEP, inputs.step_table(4))
+        done_ok = [r for r in reqs if r.error is None][-1:]
+        for r in done_ok:
+            d = srv.decode(r.result)
+            assert d.done.wait(30) and d.error is None
+            assert np.array_equal(d.result.numpy(), px_ref)
+        if server_cls is NativeServer:
+            st = srv.stats
+            assert st["cancelled"] == len(cancelled)
+            assert sum(st["latency_hist"]) >= len(reqs)
+    finally:
+        srv.close()
