@@ -381,19 +381,25 @@ def run_roundtrip(args):
         hcoef = torch.empty((n, H // 8, W // 8, 8, 8), dtype=torch.int16).pin_memory()
         himgs = [Image(hsrc[k], hdst[k], hcoef[k:k + 1]) for k in range(n)]
         harr = image_array(himgs)
-        esteps = max(3, min(args.steps, 10))
+        esteps, reps = 4, 5  # median of 5 timed windows of 4 steps (the host link is shared with other work)
         chunk = 32 << 20
         for i in range(2):
             st = lib.adct_roundtrip_host(ctx, harr, n, ctypes.byref(quants[i % len(quants)]), chunk)
             assert st == 0, lib.adct_last_error(ctx).decode()
-        d.barrier()
-        t0 = time.perf_counter()
-        for i in range(esteps):
-            st = lib.adct_roundtrip_host(ctx, harr, n, ctypes.byref(quants[i % len(quants)]), chunk)
-            assert st == 0, lib.adct_last_error(ctx).decode()
-        et = d.max(time.perf_counter() - t0)
-        e2e = {"value": d.sum(blocks * esteps) / et, "unit": "blocks/s", "h2d_bytes_per_step": n * H * W,
-               "d2h_bytes_per_step": n * H * W * 3, "steps": esteps, "api": "adct_roundtrip_host (pinned host buffers)"}
+        rates = []
+        for rep in range(reps):
+            d.barrier()
+            t0 = time.perf_counter()
+            for i in range(esteps):
+                st = lib.adct_roundtrip_host(ctx, harr, n, ctypes.byref(quants[(rep * esteps + i) % len(quants)]),
+                                             chunk)
+                assert st == 0, lib.adct_last_error(ctx).decode()
+            et = d.max(time.perf_counter() - t0)
+            rates.append(d.sum(blocks * esteps) / et)
+        e2e = {"value": statistics.median(rates), "unit": "blocks/s", "h2d_bytes_per_step": n * H * W,
+               "d2h_bytes_per_step": n * H * W * 3, "steps": esteps * reps,
+               "timing": f"median of {reps} windows of {esteps} steps", "windows": rates,
+               "api": "adct_roundtrip_host (pinned host buffers)"}
 
     cpu = None
     if not args.no_cpu and d.rank == 0 and d.ws == 1:
