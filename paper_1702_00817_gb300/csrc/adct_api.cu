@@ -249,20 +249,21 @@ adct_status check_image(const adct_image& im, int need, bool coef_only, const ch
 // Appends image im's descriptors (one per planar plane, or one for an
 // interleaved image) to out[*count..]; cpb is the number of int16
 // coefficients stored per block (64, or r when packed); plane_id numbers
-// channel 0 of the image among all planes of the call.  Returns the group:
-// 0 planar, 1 planar with edge blocks, 2 interleaved 3 channels, 3
-// interleaved 4 channels.
+// channel 0 of the image among all planes of the call.  Returns the group
+// (group_of): 0 planar, 2 interleaved 3 channels, 4 interleaved 4 channels,
+// each plus 1 when the image has edge blocks.
 int group_of(const adct_image& im, bool coef_only) {
   if (coef_only) return 0;
-  if (im.layout == ADCT_LAYOUT_INTERLEAVED) return im.channels == 3 ? 2 : 3;
-  return (im.width % 8 || im.height % 8) ? 1 : 0;
+  const int edge = (im.width % 8 || im.height % 8) ? 1 : 0;
+  if (im.layout == ADCT_LAYOUT_INTERLEAVED) return (im.channels == 3 ? 2 : 4) + edge;
+  return edge;
 }
 
 int describe_image(const adct_image& im, int32_t cpb, bool coef_only, int32_t plane_id, PlaneDesc* out,
                    int32_t* count) {
   const int32_t wb = (im.width + 7) / 8, hb = (im.height + 7) / 8;
   const int64_t nb = (int64_t)wb * hb;
-  const bool inter = group_of(im, coef_only) >= 2;
+  const bool inter = group_of(im, coef_only) >= 2;  // interleaved
   PlaneDesc d{};
   d.pitch = im.pitch;
   d.cstride = nb * cpb;
@@ -277,7 +278,7 @@ int describe_image(const adct_image& im, int32_t cpb, bool coef_only, int32_t pl
     d.plane_id = plane_id;
     d.nch = im.channels;
     out[(*count)++] = d;
-    return im.channels == 3 ? 2 : 3;
+    return group_of(im, coef_only);
   }
   for (int32_t c = 0; c < im.channels; ++c) {
     d.src = im.src ? im.src + (int64_t)c * im.plane_stride : nullptr;
@@ -287,15 +288,15 @@ int describe_image(const adct_image& im, int32_t cpb, bool coef_only, int32_t pl
     d.nch = 1;
     out[(*count)++] = d;
   }
-  return (!coef_only && (im.width % 8 || im.height % 8)) ? 1 : 0;
+  return group_of(im, coef_only);
 }
 
 // Work units of one call: one group (one launch) per pixel layout class;
-// planar images with edge blocks get their own launch so that the others run
-// kernels with the edge handling compiled out.
-constexpr int kGroups = 4;
-constexpr int kGroupNch[kGroups] = {1, 1, 3, 4};
-constexpr bool kGroupEdge[kGroups] = {false, true, true, true};
+// images with edge blocks get their own launch so that the others run kernels
+// with the edge handling compiled out.
+constexpr int kGroups = 6;
+constexpr int kGroupNch[kGroups] = {1, 1, 3, 3, 4, 4};
+constexpr bool kGroupEdge[kGroups] = {false, true, false, true, false, true};
 
 int64_t blocks_of(const adct_image& im) { return (int64_t)((im.width + 7) / 8) * ((im.height + 7) / 8); }
 

@@ -88,7 +88,8 @@ cudaError_t launch_codec(const CodecLaunch& c, const LaunchShape& shape, int sm_
   if (c.total <= 0) return cudaSuccess;
   KernelFn fn = nullptr;
   if (c.nch == 3 || c.nch == 4) {
-    fn = pick_interleaved_kernel(c.kind, c.qmode, c.evenq, c.nch);
+    fn = c.edge ? pick_interleaved_edge_kernel(c.kind, c.qmode, c.evenq, c.nch)
+                : pick_interleaved_kernel(c.kind, c.qmode, c.evenq, c.nch);
     if (!fn) return cudaErrorInvalidValue;
   } else if (c.edge) {
     fn = pick_edge_kernel(c.kind, c.qmode, c.evenq);

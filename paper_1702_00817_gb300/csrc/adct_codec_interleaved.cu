@@ -1,13 +1,13 @@
 // Codec kernels for channel-interleaved images (HWC: 3 or 4 channels per
-// pixel), every kind that reads or writes pixels, with the full zone and
-// edge handling.
+// pixel) whose sides are multiples of 8, every kind that reads or writes
+// pixels, with the full zone.
 #include "adct_codec_kernel.cuh"
 
 namespace adct {
 
 KernelFn pick_interleaved_kernel(int kind, int qmode, bool evenq, int nch) {
-  if (nch == 3) return pick_full<3, true>(kind, qmode, evenq);
-  if (nch == 4) return pick_full<4, true>(kind, qmode, evenq);
+  if (nch == 3) return pick_full<3, false>(kind, qmode, evenq);
+  if (nch == 4) return pick_full<4, false>(kind, qmode, evenq);
   return nullptr;
 }
 

@@ -1,7 +1,7 @@
 // Integer codec kernel for sm_103a (templates, instantiated by adct_codec.cu
 // for every kind and quantiser mode, by adct_codec_zonal_*.cu specialised on
 // the zonal zone, by adct_codec_edge.cu for planar images with edge blocks and
-// by adct_codec_interleaved.cu for HWC images): the blockwise 2D 14-addition
+// by adct_codec_interleaved*.cu for HWC images): the blockwise 2D 14-addition
 // transform (Sec. 2 fast algorithm T = P A3 A2 A1; Sec. 3 8x8 blocks), the
 // D^2-merged quantiser and the inverse, as one persistent kernel over a
 // flattened block index.  The path is add-only and bound by HBM bytes, so no
@@ -210,11 +210,51 @@ struct SmemPlan {
   static constexpr int warp = stages * in_stage + out_stage;
 };
 
+// A word made of bytes p0..p3 (p0 lowest) of the byte sequence held in w
+// (byte b is byte b & 3 of w[b >> 2]).  Called with constant positions inside
+// unrolled loops, so w stays in registers and each call is three PRMTs.
+__device__ __forceinline__ uint32_t pick4(const uint32_t* w, int p0, int p1, int p2, int p3) {
+  const uint32_t lo = __byte_perm(w[p0 >> 2], w[p1 >> 2], (uint32_t)((p0 & 3) | ((4 + (p1 & 3)) << 4)));
+  const uint32_t hi = __byte_perm(w[p2 >> 2], w[p3 >> 2], (uint32_t)((p2 & 3) | ((4 + (p3 & 3)) << 4)));
+  return __byte_perm(lo, hi, 0x5410);
+}
+
+// Interleaved tiles.  The input stage of a tile of 32 pixel positions holds, for
+// row i, lane l's 8 NCH interleaved bytes at (i * 32 + l) * 8 NCH (byte b of a
+// lane's row span is pixel b / NCH, channel b % NCH).  deinterleave_tile
+// rewrites it in place as NCH planar tiles: channel c's row i of lane l's
+// block at c * 2048 + (i * 32 + l) * 8, the layout of a planar tile, so the
+// blocks then run the planar code.
+template <int NCH>
+__device__ __forceinline__ void deinterleave_tile(uint8_t* stage, int lane) {
+  uint32_t w[8][2 * NCH];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const uint2* sp = (const uint2*)(stage + (i * 32 + lane) * 8 * NCH);
+#pragma unroll
+    for (int k = 0; k < NCH; ++k) {
+      const uint2 u = sp[k];
+      w[i][2 * k] = u.x;
+      w[i][2 * k + 1] = u.y;
+    }
+  }
+  __syncwarp();  // every lane has read its spans before any planar row overwrites them
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      const uint32_t a = pick4(w[i], c, c + NCH, c + 2 * NCH, c + 3 * NCH);
+      const uint32_t b = pick4(w[i], c + 4 * NCH, c + 5 * NCH, c + 6 * NCH, c + 7 * NCH);
+      ((uint2*)(stage + c * 2048))[i * 32 + lane] = make_uint2(a, b);
+    }
+}
+
 // Arithmetic of one 8x8 block: read its input from the input stage, quantise,
 // stage or store q, dequantise, invert and store the pixels.
 //
-// NCH > 1: channel ch of an interleaved image; the pixel bytes of lane l's
-// position in row i of the stage are at (i * 32 + l) * 8 NCH + NCH * j + ch.
+// NCH > 1: channel ch of an interleaved image, whose planar tile (made by
+// deinterleave_tile) starts at ch * 2048 in the stage; the reconstructed rows
+// go back to the same place.
 //
 // EDGE: the launch may contain blocks on the right or bottom edge of an image
 // whose side is not a multiple of 8 (compiled out of the launches that have
@@ -235,8 +275,8 @@ __device__ __forceinline__ uint32_t block_step(uint8_t* __restrict__ in, uint8_t
   // the input stage already holds the last valid row in place of the others)
   const int vc = EDGE ? valid_cols(d, pos) : 8, vr = EDGE ? valid_rows(d, pos) : 8;
   int32_t v[64];
-  if (KT::in_pix && NCH == 1) {
-    const uint2* st = (const uint2*)in;
+  if (KT::in_pix) {
+    const uint2* st = (const uint2*)(in + (NCH > 1 ? ch * 2048 : 0));
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const uint2 w = st[i * 32 + lane];
@@ -245,19 +285,12 @@ __device__ __forceinline__ uint32_t block_step(uint8_t* __restrict__ in, uint8_t
         v[8 * i + j] = (int32_t)__byte_perm(w.x, 0u, 0x4440 | j);
         v[8 * i + 4 + j] = (int32_t)__byte_perm(w.y, 0u, 0x4440 | j);
       }
-      if (EDGE) {
+      if (EDGE) {  // branch-free: a per-lane branch here measured slower
 #pragma unroll
         for (int j = 1; j < 8; ++j) v[8 * i + j] = j < vc ? v[8 * i + j] : v[8 * i + j - 1];
       }
     }
     fwd2d(v);  // Z + 8192 e0 e0^T (raw pixels; the level shift lives in the constants)
-  } else if (KT::in_pix) {
-    const uint8_t* px = in + lane * 8 * NCH + ch;  // channel ch's bytes, NCH apart
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-      for (int j = 0; j < 8; ++j) v[8 * i + j] = px[i * 256 * NCH + NCH * (EDGE ? min(j, vc - 1) : j)];
-    fwd2d(v);
   } else if (QMODE == QM_ZONAL_ZZ) {
     // packed input: the first r zig-zag coefficients of this block
     constexpr ZigZag zz = make_zigzag();
@@ -356,9 +389,9 @@ __device__ __forceinline__ uint32_t block_step(uint8_t* __restrict__ in, uint8_t
   uint32_t err = 0;
   if (KT::inv) {
     inv2d(v);
-    if (KT::sse && NCH == 1) {
+    if (KT::sse) {
       // squared error against the input rows, still in the input stage
-      const uint2* st = (const uint2*)in;
+      const uint2* st = (const uint2*)(in + (NCH > 1 ? ch * 2048 : 0));
       const uint32_t m0 = vc >= 4 ? 0xffffffffu : (1u << (8 * vc)) - 1u;
       const uint32_t m1 = vc >= 8 ? 0xffffffffu : vc <= 4 ? 0u : (1u << (8 * (vc - 4))) - 1u;
 #pragma unroll
@@ -369,22 +402,6 @@ __device__ __forceinline__ uint32_t block_step(uint8_t* __restrict__ in, uint8_t
         if (i < vr) {
           err = __dp4a(e0, e0, err);
           err = __dp4a(e1, e1, err);
-        }
-      }
-    } else if (KT::sse) {
-      const uint8_t* px = in + lane * 8 * NCH + ch;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-#pragma unroll
-        for (int j4 = 0; j4 < 2; ++j4) {
-          const uint32_t w = pixels4(v[8 * i + 4 * j4], v[8 * i + 4 * j4 + 1], v[8 * i + 4 * j4 + 2],
-                                     v[8 * i + 4 * j4 + 3]);
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const int j = 4 * j4 + b;
-            const int e = (int)((w >> (8 * b)) & 0xffu) - (int)px[i * 256 * NCH + NCH * j];
-            if (i < vr && j < vc) err += (uint32_t)(e * e);
-          }
         }
       }
     } else if (NCH == 1) {
@@ -403,27 +420,24 @@ __device__ __forceinline__ uint32_t block_step(uint8_t* __restrict__ in, uint8_t
         }
       }
     } else {
-      // interleaved: channel ch's bytes back into the stage, stored by the warp
-      uint8_t* px = in + lane * 8 * NCH + ch;
+      // interleaved: the reconstructed rows back into this channel's planar
+      // tile (its input is consumed), interleaved and stored once every
+      // channel is done
+      uint2* pl = (uint2*)(in + ch * 2048);
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-#pragma unroll
-        for (int j4 = 0; j4 < 2; ++j4) {
-          const uint32_t w = pixels4(v[8 * i + 4 * j4], v[8 * i + 4 * j4 + 1], v[8 * i + 4 * j4 + 2],
-                                     v[8 * i + 4 * j4 + 3]);
-#pragma unroll
-          for (int b = 0; b < 4; ++b) px[i * 256 * NCH + NCH * (4 * j4 + b)] = (uint8_t)(w >> (8 * b));
-        }
-      }
+      for (int i = 0; i < 8; ++i)
+        pl[i * 32 + lane] = make_uint2(pixels4(v[8 * i + 0], v[8 * i + 1], v[8 * i + 2], v[8 * i + 3]),
+                                       pixels4(v[8 * i + 4], v[8 * i + 5], v[8 * i + 6], v[8 * i + 7]));
     }
   }
   return err;
 }
 
 // Store the reconstructed interleaved pixels of a 32-position tile from its
-// stage: lane l writes its 8 NCH bytes of each valid row (NCH 8-byte stores,
-// so the warp covers 256 NCH contiguous bytes per row), byte by byte on the
-// image's right edge.
+// NCH planar tiles: each row's channel words are interleaved in registers
+// (byte b of the span is byte (b / NCH) & 3 of channel b % NCH's word
+// (b / NCH) / 4) and written with NCH 8-byte stores, so the warp covers 256 NCH
+// contiguous bytes per row; byte by byte on the image's right edge.
 template <int NCH, bool EDGE>
 __device__ __forceinline__ void write_pixels_interleaved(const uint8_t* __restrict__ stage,
                                                         const PlaneDesc* __restrict__ planes, const Pos& pos,
@@ -433,14 +447,34 @@ __device__ __forceinline__ void write_pixels_interleaved(const uint8_t* __restri
   const int64_t pitch = __ldg(&d->pitch);
   uint8_t* o = dst_of(d) + (int64_t)(8 * pos.by) * pitch + 8 * NCH * pos.bx;
   const int vc = EDGE ? valid_cols(d, pos) : 8, vr = EDGE ? valid_rows(d, pos) : 8;
-  const uint8_t* sp = stage + lane * 8 * NCH;
-  for (int i = 0; i < vr; ++i) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    if (i >= vr) break;
+    uint32_t q[2 * NCH];  // channel c's pixels 0-3 and 4-7 at q[2c], q[2c + 1]
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      const uint2 u = ((const uint2*)(stage + c * 2048))[i * 32 + lane];
+      q[2 * c] = u.x;
+      q[2 * c + 1] = u.y;
+    }
+    uint32_t span[2 * NCH];
+#pragma unroll
+    for (int m = 0; m < 2 * NCH; ++m) {
+      int pos4[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int b = 4 * m + t, px = b / NCH, c = b % NCH;
+        pos4[t] = 4 * (2 * c + (px >> 2)) + (px & 3);
+      }
+      span[m] = pick4(q, pos4[0], pos4[1], pos4[2], pos4[3]);
+    }
     if (vc == 8) {
 #pragma unroll
-      for (int k = 0; k < NCH; ++k)
-        __stcs((uint2*)(o + i * pitch) + k, *(const uint2*)(sp + i * 256 * NCH + 8 * k));
+      for (int k = 0; k < NCH; ++k) __stcs((uint2*)(o + i * pitch) + k, make_uint2(span[2 * k], span[2 * k + 1]));
     } else {
-      for (int b = 0; b < NCH * vc; ++b) o[i * pitch + b] = sp[i * 256 * NCH + b];
+#pragma unroll
+      for (int b = 0; b < 8 * NCH; ++b)
+        if (b < NCH * vc) o[i * pitch + b] = (uint8_t)(span[b >> 2] >> (8 * (b & 3)));
     }
   }
 }
@@ -647,6 +681,10 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
 
     const Pos pc = ring[0];
     uint8_t* stage = wsm + s * SP::in_stage;
+    if (NCH > 1 && KT::in_pix) {
+      deinterleave_tile<NCH>(stage, lane);
+      __syncwarp();
+    }
     if (KT::sse && pc.plane >= 0 && pc.plane != acc_plane) {  // one atomic per lane and channel per plane visited
       flush();
       acc_plane = pc.plane;

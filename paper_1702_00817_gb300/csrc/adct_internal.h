@@ -54,9 +54,11 @@ enum CheckedFault : unsigned int { FAULT_POSITION = 1u, FAULT_ROW_BYTES = 2u };
 // kind / mode pair has no specialisation.
 KernelFn pick_zonal_kernel_lo(int kind, int qmode, int zs);
 KernelFn pick_zonal_kernel_hi(int kind, int qmode, int zs);
-// Kernels for interleaved images of nch = 3 or 4 channels
-// (adct_codec_interleaved.cu); nullptr for kinds without one.
+// Kernels for interleaved images of nch = 3 or 4 channels, without and with
+// edge blocks (adct_codec_interleaved.cu, adct_codec_interleaved_edge.cu);
+// nullptr for kinds without one.
 KernelFn pick_interleaved_kernel(int kind, int qmode, bool evenq, int nch);
+KernelFn pick_interleaved_edge_kernel(int kind, int qmode, bool evenq, int nch);
 // Kernels for planar images with edge blocks (adct_codec_edge.cu).
 KernelFn pick_edge_kernel(int kind, int qmode, bool evenq);
 
