@@ -25,8 +25,9 @@
 //     128-byte line instead of one per 16 bytes); packed zonal coefficients
 //     are staged per lane and written back as one contiguous range;
 //   - reconstructed pixels are stored directly (256 contiguous bytes per warp
-//     instruction already), or, for interleaved images, written back into the
-//     input stage and stored by the warp once every channel is done.
+//     instruction already), or, for interleaved images, put back into the
+//     channels' planar tiles and stored by each lane as re-interleaved rows
+//     once every channel is done.
 //
 // Arithmetic per block (one lane):
 //   forward  raw bytes -> 8 row butterflies -> 8 column butterflies (Z + 8192 e0e0^T);
@@ -197,10 +198,10 @@ constexpr int kTile = 32;
 // least arithmetic per block slower by up to 20 % at the same occupancy.
 //
 // NCH > 1 (interleaved images): a tile is 32 pixel positions of NCH channels;
-// its input stage holds the 8 rows of 32 x 8 NCH interleaved bytes, and the
-// reconstructed pixels are written back into the same stage (a channel's
-// bytes once that channel's block is in registers) before the warp stores
-// them.  The inverse from coefficients uses the stage only for that.
+// its input stage holds the 8 rows of 32 x 8 NCH interleaved bytes, rewritten
+// in place as NCH planar tiles of 2 KB; each channel's reconstruction goes back
+// into its planar tile before the rows are re-interleaved and stored.  The
+// inverse from coefficients uses the stage only for the reconstruction.
 template <int KIND, int NCH = 1>
 struct SmemPlan {
   static constexpr int stages = 2;
