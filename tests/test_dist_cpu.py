@@ -4,7 +4,6 @@ sum of units over the slowest rank's time."""
 import os
 import socket
 
-import pytest
 import torch.multiprocessing as mp
 
 
