@@ -205,7 +205,21 @@ class Codec:
         N.check(self.lib.adct_get_launch(self.ctx, ctypes.byref(l)), self.ctx, "adct_get_launch", lib=self.lib)
         return {f: getattr(l, f) for f, _ in N.adct_launch._fields_}
 
-    def autotune(self, images, quant, reps: int = 5, stream=None):
+    def autotune(self, images, quant, reps: int = 5, stream=None, cache: str | None = None):
+        """Pick the fastest launch shape for this batch (adct_autotune) and keep it
+        in the context.  cache: a JSON file of earlier results keyed by the
+        batch signature (device, image shapes and layouts, which outputs,
+        quantiser); a hit applies the stored shape without measuring.  Returns
+        (shape, mean microseconds; None on a cache hit)."""
+        key = self._signature(images, quant) if cache else None
+        if cache:
+            import json
+            import os
+            table = json.load(open(cache)) if os.path.exists(cache) else {}
+            if key in table:
+                shape = table[key]["launch"]
+                self.set_launch(shape["threads_per_cta"], shape["ctas_per_sm"] or -1, shape["stage_coef"])
+                return shape, None
         arr = image_array(images, quant)
         best = N.adct_launch()
         us = ctypes.c_float(0)
@@ -213,7 +227,24 @@ class Codec:
                                     _stream_handle(self.device, stream), int(reps), ctypes.byref(best),
                                     ctypes.byref(us))
         N.check(st, self.ctx, "adct_autotune", lib=self.lib)
-        return {f: getattr(best, f) for f, _ in N.adct_launch._fields_}, us.value
+        shape = {f: getattr(best, f) for f, _ in N.adct_launch._fields_}
+        if cache:
+            table = json.load(open(cache)) if os.path.exists(cache) else {}
+            table[key] = {"launch": shape, "us": us.value}
+            tmp = f"{cache}.{os.getpid()}.tmp"
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return shape, us.value
+
+    def _signature(self, images, quant) -> str:
+        import hashlib
+        parts = [torch.cuda.get_device_name(self.device), f"mode={quant.mode} r={quant.r}"]
+        for im in images:
+            im = Image(*im) if isinstance(im, (tuple, list)) else im
+            s = image_struct(im, coef_per_block(quant))
+            parts.append(f"{s.width}x{s.height}x{s.channels}/{s.layout}/{int(bool(s.coef))}{int(bool(s.dst))}")
+        return hashlib.sha256("|".join(parts).encode()).hexdigest()[:24]
 
     def roundtrip_host(self, images, quant, chunk_bytes: int = 32 << 20):
         """End-to-end round trip on host (ideally pinned) tensors; synchronous."""

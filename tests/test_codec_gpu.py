@@ -391,3 +391,24 @@ def test_full_size_uniform_batch(codec, mode, Q, r):
     with ThreadPoolExecutor(max_workers=os.cpu_count() or 8) as ex:
         ok = list(ex.map(same, range(n)))
     assert all(ok), [k for k, o in enumerate(ok) if not o][:10]
+
+
+def test_autotune_cache_file(codec, tmp_path):
+    imgs = [inputs.synth_image(128, 192, 40 + k)[0] for k in range(3)]
+    srcs = [_dev_img(x) for x in imgs]
+    ims = [Image(s, torch.empty_like(s), None) for s in srcs]
+    Q = make_quant(ADCT_Q_STEP, inputs.step_table(4))
+    path = str(tmp_path / "tune.json")
+    before = codec.get_launch()
+    shape, us = codec.autotune(ims, Q, reps=1, cache=path)
+    assert us is not None and us > 0 and os.path.exists(path)
+    codec.set_launch(32, 2, 0)  # something else
+    shape2, us2 = codec.autotune(ims, Q, reps=1, cache=path)  # a hit: nothing measured
+    assert us2 is None and shape2 == shape
+    got = codec.get_launch()
+    assert got["threads_per_cta"] == shape["threads_per_cta"] and got["stage_coef"] == shape["stage_coef"]
+    codec.roundtrip(ims, Q)
+    torch.cuda.synchronize()
+    for x, im in zip(imgs, ims):
+        assert np.array_equal(im.dst.cpu().numpy(), oracle.roundtrip(x, oracle.MODE_STEP, inputs.step_table(4))[1])
+    codec.set_launch(before["threads_per_cta"], before["ctas_per_sm"] or -1, before["stage_coef"])
