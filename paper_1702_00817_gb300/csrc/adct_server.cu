@@ -170,16 +170,14 @@ int latency_bucket(double seconds) {
   return b;
 }
 
-// Reports a request's completion.  locked: the caller holds s->mu.
-void complete(adct_server* s, const Req& r, int32_t status, double t_done, bool locked = false) {
-  if (locked) {
-    s->pending.erase(r.id);
-    s->cancelled.erase(r.id);
-  } else {
-    std::lock_guard<std::mutex> lk(s->mu);
-    s->pending.erase(r.id);
-    s->cancelled.erase(r.id);
-  }
+// Drops a finished request from the pending and cancelled sets (caller holds s->mu).
+void forget(adct_server* s, const Req& r) {
+  s->pending.erase(r.id);
+  if (!s->cancelled.empty()) s->cancelled.erase(r.id);
+}
+
+// Reports a request's completion (the caller has already forgotten it).
+void complete(adct_server* s, const Req& r, int32_t status, double t_done) {
   ++s->s_hist[latency_bucket(t_done - r.t_submit)];
   adct_completion c{};
   c.request_id = r.id;
@@ -225,6 +223,7 @@ void retire(adct_server* s) {
       std::lock_guard<std::mutex> lk(s->mu);
       for (const Req& r : b.reqs) {
         s->arena.free(r.tmp_off, r.tmp_bytes);
+        forget(s, r);
         auto it = s->store.find(r.handle);
         if (r.kind == KIND_ENCODE) {
           if (it != s->store.end()) it->second.ready = true;
@@ -274,7 +273,8 @@ void admit(adct_server* s, std::vector<Req>& enc, std::vector<Req>& dec) {
         if (it != s->store.end()) --it->second.refs;
       }
       ++s->s_cancelled;
-      complete(s, r, ADCT_ERR_CANCELLED, now_s(), true);
+      forget(s, r);
+      complete(s, r, ADCT_ERR_CANCELLED, now_s());
     }
     s->queue.swap(keep);
   }
@@ -287,7 +287,8 @@ void admit(adct_server* s, std::vector<Req>& enc, std::vector<Req>& dec) {
         Req gone = r;
         s->queue.pop_front();
         ++s->s_unknown;
-        complete(s, gone, ADCT_ERR_INVALID_ARG, now_s(), true);
+        forget(s, gone);
+        complete(s, gone, ADCT_ERR_INVALID_ARG, now_s());
         continue;
       }
       if (!it->second.ready) break;  // its encode is still running: keep FIFO order
@@ -298,7 +299,8 @@ void admit(adct_server* s, std::vector<Req>& enc, std::vector<Req>& dec) {
       Req big = r;
       s->queue.pop_front();
       ++s->s_oversized;
-      complete(s, big, ADCT_ERR_OOM, now_s(), true);
+      forget(s, big);
+      complete(s, big, ADCT_ERR_OOM, now_s());
       continue;
     }
     size_t off_tmp = s->arena.alloc(pix), off_coef = SIZE_MAX;
@@ -389,6 +391,7 @@ void launch(adct_server* s, std::vector<Req>& reqs, int kind) {
     std::lock_guard<std::mutex> lk(s->mu);
     for (const Req& r : b.reqs) {
       s->arena.free(r.tmp_off, r.tmp_bytes);
+      forget(s, r);
       auto it = s->store.find(r.handle);
       if (it == s->store.end()) continue;
       if (r.kind == KIND_ENCODE) {
@@ -594,7 +597,8 @@ adct_status adct_server_cancel(adct_server* s, uint64_t request_id) {
       if (e != s->store.end()) --e->second.refs;
     }
     ++s->s_cancelled;
-    complete(s, r, ADCT_ERR_CANCELLED, now_s(), true);
+    forget(s, r);
+    complete(s, r, ADCT_ERR_CANCELLED, now_s());
     return ADCT_OK;
   }
   s->cancelled.insert(request_id);  // in the scheduler's queue, or already admitted
