@@ -194,7 +194,7 @@ adct_status build_quant(adct_context* ctx, const adct_quant* q, bool pixel_input
     qp.c[k] = 0;
     qp.magic[k] = 0;
     qp.K[k] = 0;
-    qp.sflag[k] = 0;
+    qp.ssel[k] = 0x4444u;
     const int32_t bias = (k == 0) ? 8224 : 0;  // 32 + 128 * 64
     if (!uses_step(q->mode)) {
       qp.w[k] = 1 << shift;
@@ -210,7 +210,7 @@ adct_status build_quant(adct_context* ctx, const adct_quant* q, bool pixel_input
     qp.K[k] = K;
     qp.c[k] = zoff + (int32_t)(Q / 2) + K * (int32_t)Q + (Q == 1 ? 1 : 0);
     qp.magic[k] = (Q == 1) ? 0xFFFFFFFFu : (uint32_t)(((1ull << 32) + Q - 1) / Q);
-    qp.sflag[k] = (Q % 2 == 0) ? -1 : 0;
+    qp.ssel[k] = (Q % 2 == 0) ? 0xBBBBu : 0x4444u;
     if (Q % 2 == 0) evenq = true;
     qp.kw[k] = (int32_t)((uint32_t)bias - (uint32_t)K * (uint32_t)qp.w[k]);
   }

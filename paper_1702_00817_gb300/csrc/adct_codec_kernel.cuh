@@ -58,6 +58,14 @@ __device__ __forceinline__ int32_t sext_hi16(uint32_t w) { return ((int32_t)w) >
 __device__ __forceinline__ uint32_t pack16(int32_t lo, int32_t hi) {
   return __byte_perm((uint32_t)lo, (uint32_t)hi, 0x5410);
 }
+// One byte permute: selector 0xBBBB gives -1 for x < 0 and 0 otherwise (the
+// sign of byte 3 replicated into every byte), 0x4444 gives 0 (a byte of the
+// zero operand).
+__device__ __forceinline__ int32_t sign_sel(int32_t x, uint32_t sel) {
+  uint32_t r;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(0u), "r"(sel));
+  return (int32_t)r;
+}
 // (c << 16) | (sat_u8(a) << 8) | sat_u8(b)
 __device__ __forceinline__ uint32_t cvt_pack_u8(int32_t a, int32_t b, uint32_t c) {
   uint32_t d;
@@ -358,7 +366,7 @@ __device__ __forceinline__ uint32_t block_step(uint8_t* __restrict__ in, uint8_t
         v[k] = (int32_t)((uint32_t)((z + zoff) & qp.keep[k]) * (uint32_t)qp.w[k] + (uint32_t)bias);
       } else if (QMODE == QM_STEP || QMODE == QM_STEP_ZONAL) {
         int32_t n = z + qp.c[k];
-        if (EVENQ) n += ((z + zoff) >> 31) & qp.sflag[k];
+        if (EVENQ) n += sign_sel(z + zoff, qp.ssel[k]);
         const uint32_t m = __umulhi((uint32_t)n, qp.magic[k]);
         int32_t qq = (int32_t)m - qp.K[k];
         if (QMODE == QM_STEP_ZONAL) qq &= qp.keep[k];

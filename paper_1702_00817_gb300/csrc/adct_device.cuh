@@ -128,7 +128,9 @@ static_assert(sizeof(PlaneDesc) == 64, "descriptor layout");
 // instruction operands.  For position k = 8i + j with step Q:
 //   STEP (Q <= 16384): n = Z + c with c = floor(Q/2) + K*Q (+1 when Q = 1), where
 //     K = ceil(8193 / Q) keeps n in [0, 2^16); when Q is even and Z < 0 the
-//     bias drops by one (sflag = -1) so that ties round away from zero.
+//     bias drops by one so that ties round away from zero: ssel is the byte
+//     selector 0xBBBB (every byte the sign of byte 3: -1 for Z < 0, else 0)
+//     for even Q and 0x4444 (a zero byte: no correction) otherwise.
 //     m = umulhi(n, magic) = floor(n / Q) exactly (magic = ceil(2^32 / Q), or
 //     2^32 - 1 with the +1 above for Q = 1; exact for n < 2^16, Q <= 2^16),
 //     q = m - K = sgn(Z) floor((|Z| + floor(Q/2)) / Q) = round half away from zero of Z / Q.
@@ -143,7 +145,7 @@ struct QuantParams {
   int32_t c[64];
   uint32_t magic[64];
   int32_t K[64];
-  int32_t sflag[64];
+  uint32_t ssel[64];
   int32_t w[64];
   int32_t kw[64];
   int32_t keep[64];
