@@ -804,10 +804,12 @@ def run_serving(args):
             wall = max(r.t_done for r in reqs) - t0
             ok = [r for r in reqs if r.error is None]
             lat = np.array([r.latency for r in ok]) * 1000.0
+            late = np.array([r.t_sent - r.t_arrival for r in reqs]) * 1000.0  # client lateness, inside the latency
             px = sum(r.pixels.numel() if r.kind == "encode" else r.out_pixels for r in ok)
             rows.append({"offered_req_s": rate, "req_s": len(ok) / wall, "p50_ms": float(np.percentile(lat, 50)),
                          "p99_ms": float(np.percentile(lat, 99)), "errors": len(reqs) - len(ok),
-                         "blocks_s": px / 64 / wall})
+                         "blocks_s": px / 64 / wall, "client_late_p99_ms": float(np.percentile(late, 99)),
+                         "client_late_max_ms": float(late.max())})
         gc.enable()
         results[name] = {"rows": rows, "stats": dict(srv.stats)}
         srv.close()

@@ -36,6 +36,7 @@ class Request:
     pixels: torch.Tensor | None = None   # encode: host uint8 [H, W] (pinned is fastest)
     handle: int | None = None       # decode: store handle
     t_arrival: float = 0.0
+    t_sent: float = 0.0             # poisson_run: when the client handed it to submit (>= t_arrival)
     t_admit: float = 0.0
     t_done: float = 0.0
     result: object = None           # encode: handle; decode: host uint8 [H, W]
@@ -366,6 +367,7 @@ def poisson_run(server, rate: float, n_requests: int, sizes, images_by_size, see
         else:
             r = Request("decode", handle=live[int(rng.integers(0, len(live)))], t_arrival=t)
             pending_dec.append(r)
+        r.t_sent = time.perf_counter()
         server.submit(r)
         reqs.append(r)
     for r in reqs:
