@@ -112,6 +112,36 @@ def test_degenerate_shapes(codec):
     _check_roundtrip(codec, imgs, ADCT_Q_STEP, inputs.step_table(4))
 
 
+def test_maximum_sides_and_64bit_offsets(codec):
+    """The longest sides the ABI accepts (65536) against the oracle in full,
+    and a 40000 x 65536 image (2.6 GB of pixels, 5.2 GB of coefficients) whose
+    byte offsets pass 2^31 on sampled blocks: every 8x8 block is independent,
+    so the oracle runs on the block alone; the samples include the four
+    corner blocks."""
+    _check_roundtrip(codec, [inputs.synth_image(8, 65536, 5)[0], inputs.synth_image(65536, 8, 6)[0]], ADCT_Q_STEP,
+                     inputs.step_table(4))
+    H, W = 40000, 65536
+    g = torch.Generator(device=DEV)
+    g.manual_seed(1702)
+    src = torch.randint(0, 256, (H, W), dtype=torch.uint8, device=DEV, generator=g)
+    dst = torch.empty_like(src)
+    coef = torch.empty((1, H // 8, W // 8, 8, 8), dtype=torch.int16, device=DEV)
+    Qt = inputs.step_table(4)
+    codec.roundtrip([Image(src, dst, coef)], make_quant(ADCT_Q_STEP, Qt))
+    torch.cuda.synchronize()
+    hb, wb = H // 8, W // 8
+    rng = np.random.default_rng(7)
+    picks = [(hb - 1, wb - 1), (hb - 1, 0), (0, wb - 1), (0, 0)]
+    picks += [(int(rng.integers(hb)), int(rng.integers(wb))) for _ in range(60)]
+    for by, bx in picks:
+        blk = src[8 * by:8 * by + 8, 8 * bx:8 * bx + 8].cpu().numpy()
+        q_ref, rec_ref = oracle.roundtrip(blk, oracle.MODE_STEP, Qt, 64)
+        assert np.array_equal(dst[8 * by:8 * by + 8, 8 * bx:8 * bx + 8].cpu().numpy(), rec_ref), (by, bx)
+        assert np.array_equal(coef[0, by, bx].cpu().numpy().astype(np.int64), q_ref[0, 0]), (by, bx)
+    del src, dst, coef
+    torch.cuda.empty_cache()
+
+
 def test_ragged_multichannel_batch_one_launch(codec):
     sizes = inputs.ragged_sizes(12, seed=11, lo_log2=3.0, hi_log2=8.0)
     imgs = inputs.ragged_batch(sizes, channels=3, base_seed=50)

@@ -257,6 +257,42 @@ def test_layout_errors(codec):
     assert e.value.status == _native.ADCT_ERR_ALIGN
 
 
+def test_large_interleaved_edge_image_sampled(codec):
+    """An interleaved 11999 x 65535 x 3 image (2.4 GB: pixel offsets past 2^31
+    bytes, an edge block at the end of every block row and in the last block
+    row), step s = 4, on sampled blocks of every channel: the oracle runs on
+    the block alone, edge-extended like the image."""
+    H, W = 11999, 65535
+    pitch = (W * 3 + 7) // 8 * 8
+    g = torch.Generator(device=DEV)
+    g.manual_seed(1703)
+    buf = torch.randint(0, 256, (H, pitch), dtype=torch.uint8, device=DEV, generator=g)
+    src = buf[:, :W * 3].view(H, W, 3)
+    out = torch.empty_like(buf)
+    dst = out[:, :W * 3].view(H, W, 3)
+    hb, wb = (H + 7) // 8, (W + 7) // 8
+    coef = torch.empty((3, hb, wb, 8, 8), dtype=torch.int16, device=DEV)
+    Qt = inputs.step_table(4)
+    codec.roundtrip([Image(src, dst, coef, True)], make_quant(ADCT_Q_STEP, Qt))
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(8)
+    picks = [(hb - 1, wb - 1), (hb - 1, 0), (0, wb - 1), (0, 0), (hb - 2, wb - 1), (hb - 1, wb - 2)]
+    picks += [(int(rng.integers(hb)), int(rng.integers(wb))) for _ in range(40)]
+    for by, bx in picks:
+        y0, x0 = 8 * by, 8 * bx
+        vr, vc = min(8, H - y0), min(8, W - x0)
+        blk = src[y0:y0 + vr, x0:x0 + vc].cpu().numpy()
+        got = dst[y0:y0 + vr, x0:x0 + vc].cpu().numpy()
+        cf = coef[:, by, bx].cpu().numpy().astype(np.int64)
+        for c in range(3):
+            padded = np.pad(blk[:, :, c], ((0, 8 - vr), (0, 8 - vc)), mode="edge")
+            q_ref, rec_ref = oracle.roundtrip(padded, oracle.MODE_STEP, Qt, 64)
+            assert np.array_equal(got[:, :, c], rec_ref[:vr, :vc]), (by, bx, c)
+            assert np.array_equal(cf[c], q_ref[0, 0]), (by, bx, c)
+    del buf, out, coef
+    torch.cuda.empty_cache()
+
+
 def test_full_hd_rgb_batch_sampled(codec):
     """16 interleaved 1080x1920x3 images in one launch, sampled channels
     against the oracle (the 1080-row edge is a multiple of 8; 1917 columns
