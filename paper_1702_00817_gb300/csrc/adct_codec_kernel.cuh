@@ -286,17 +286,27 @@ __device__ __forceinline__ uint32_t block_step(uint8_t* __restrict__ in, uint8_t
   int32_t v[64];
   if (KT::in_pix) {
     const uint2* st = (const uint2*)(in + (NCH > 1 ? ch * 2048 : 0));
+    // Edge blocks: byte j of each row becomes byte min(j, vc - 1), one byte
+    // permute per 4 bytes (selector nibble j = min(j, vc - 1); the identity
+    // for full blocks).
+    uint32_t sel = 0x76543210u;
+    if (EDGE) {
+      const uint32_t c = (uint32_t)vc - 1u;
+      const uint32_t hi = c >= 7u ? 0u : 0xFFFFFFFFu << (4u * (c + 1u));  // nibbles above c
+      sel = (sel & ~hi) | (c * 0x11111111u & hi);
+    }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const uint2 w = st[i * 32 + lane];
+      uint2 w = st[i * 32 + lane];
+      if (EDGE) {
+        const uint2 raw = w;
+        w.x = __byte_perm(raw.x, raw.y, sel & 0xFFFFu);
+        w.y = __byte_perm(raw.x, raw.y, sel >> 16);
+      }
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         v[8 * i + j] = (int32_t)__byte_perm(w.x, 0u, 0x4440 | j);
         v[8 * i + 4 + j] = (int32_t)__byte_perm(w.y, 0u, 0x4440 | j);
-      }
-      if (EDGE) {  // branch-free: a per-lane branch here measured slower
-#pragma unroll
-        for (int j = 1; j < 8; ++j) v[8 * i + j] = j < vc ? v[8 * i + j] : v[8 * i + j - 1];
       }
     }
     fwd2d(v);  // Z + 8192 e0 e0^T (raw pixels; the level shift lives in the constants)
@@ -425,7 +435,9 @@ __device__ __forceinline__ uint32_t block_step(uint8_t* __restrict__ in, uint8_t
         if (!edge) {
           __stcs((uint2*)(o + i * pitch), w);
         } else if (i < vr) {
-          for (int j = 0; j < vc; ++j) o[i * pitch + j] = (uint8_t)((j < 4 ? w.x >> (8 * j) : w.y >> (8 * (j - 4))));
+          const uint64_t row = ((uint64_t)w.y << 32) | w.x;
+#pragma unroll 1
+          for (int j = 0; j < vc; ++j) o[i * pitch + j] = (uint8_t)(row >> (8 * j));
         }
       }
     } else {
@@ -482,8 +494,12 @@ __device__ __forceinline__ void write_pixels_interleaved(const uint8_t* __restri
       for (int k = 0; k < NCH; ++k) __stcs((uint2*)(o + i * pitch) + k, make_uint2(span[2 * k], span[2 * k + 1]));
     } else {
 #pragma unroll
-      for (int b = 0; b < 8 * NCH; ++b)
-        if (b < NCH * vc) o[i * pitch + b] = (uint8_t)(span[b >> 2] >> (8 * (b & 3)));
+      for (int k = 0; k < NCH; ++k) {
+        const uint64_t part = ((uint64_t)span[2 * k + 1] << 32) | span[2 * k];
+        const int nb = min(8, NCH * vc - 8 * k);  // valid bytes of this 8-byte part
+#pragma unroll 1
+        for (int j = 0; j < nb; ++j) o[i * pitch + 8 * k + j] = (uint8_t)(part >> (8 * j));
+      }
     }
   }
 }
