@@ -78,6 +78,27 @@ __device__ __forceinline__ uint32_t pixels4(int32_t r0, int32_t r1, int32_t r2, 
   return cvt_pack_u8(r1 >> 6, r0 >> 6, hi);
 }
 
+// Bytes [0, n) of the little-endian 8-byte row r to p (8-byte aligned),
+// 0 <= n <= 8: at most three stores (4, 2 and 1 bytes, each aligned).
+__device__ __forceinline__ void store_prefix8(uint8_t* p, uint64_t r, int n) {
+  if (n >= 8) {
+    *(uint2*)p = make_uint2((uint32_t)r, (uint32_t)(r >> 32));
+    return;
+  }
+  int off = 0;
+  if (n & 4) {
+    *(uint32_t*)p = (uint32_t)r;
+    r >>= 32;
+    off = 4;
+  }
+  if (n & 2) {
+    *(uint16_t*)(p + off) = (uint16_t)r;
+    r >>= 16;
+    off += 2;
+  }
+  if (n & 1) p[off] = (uint8_t)r;
+}
+
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -426,19 +447,19 @@ __device__ __forceinline__ uint32_t block_step(uint8_t* __restrict__ in, uint8_t
     } else if (NCH == 1) {
       const int64_t pitch = __ldg(&d->pitch);
       uint8_t* o = dst_of(d) + (int64_t)(8 * pos.by) * pitch + 8 * pos.bx;
-      const bool edge = (vc < 8) | (vr < 8);
+      uint2 w[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        uint2 w;
-        w.x = pixels4(v[8 * i + 0], v[8 * i + 1], v[8 * i + 2], v[8 * i + 3]);
-        w.y = pixels4(v[8 * i + 4], v[8 * i + 5], v[8 * i + 6], v[8 * i + 7]);
-        if (!edge) {
-          __stcs((uint2*)(o + i * pitch), w);
-        } else if (i < vr) {
-          const uint64_t row = ((uint64_t)w.y << 32) | w.x;
-#pragma unroll 1
-          for (int j = 0; j < vc; ++j) o[i * pitch + j] = (uint8_t)(row >> (8 * j));
-        }
+        w[i].x = pixels4(v[8 * i + 0], v[8 * i + 1], v[8 * i + 2], v[8 * i + 3]);
+        w[i].y = pixels4(v[8 * i + 4], v[8 * i + 5], v[8 * i + 6], v[8 * i + 7]);
+      }
+      if (!EDGE || ((vc == 8) & (vr == 8))) {  // one branch per block, not per row
+#pragma unroll
+        for (int i = 0; i < 8; ++i) __stcs((uint2*)(o + i * pitch), w[i]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (i < vr) store_prefix8(o + i * pitch, ((uint64_t)w[i].y << 32) | w[i].x, vc);
       }
     } else {
       // interleaved: the reconstructed rows back into this channel's planar
@@ -494,12 +515,9 @@ __device__ __forceinline__ void write_pixels_interleaved(const uint8_t* __restri
       for (int k = 0; k < NCH; ++k) __stcs((uint2*)(o + i * pitch) + k, make_uint2(span[2 * k], span[2 * k + 1]));
     } else {
 #pragma unroll
-      for (int k = 0; k < NCH; ++k) {
-        const uint64_t part = ((uint64_t)span[2 * k + 1] << 32) | span[2 * k];
-        const int nb = min(8, NCH * vc - 8 * k);  // valid bytes of this 8-byte part
-#pragma unroll 1
-        for (int j = 0; j < nb; ++j) o[i * pitch + 8 * k + j] = (uint8_t)(part >> (8 * j));
-      }
+      for (int k = 0; k < NCH; ++k)  // valid bytes of each 8-byte part
+        store_prefix8(o + i * pitch + 8 * k, ((uint64_t)span[2 * k + 1] << 32) | span[2 * k],
+                      max(0, NCH * vc - 8 * k));
     }
   }
 }
