@@ -196,12 +196,18 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash() -> str:
-    """Hash of the codec kernel's code (line comments and blank lines left out,
+KERNEL_SOURCES = {
+    "codec": ("adct_codec_kernel.cuh", "adct_codec.cu", "adct_device.cuh", "adct_codec_zonal_lo.cu",
+              "adct_codec_zonal_hi.cu"),
+    "float": ("adct_float.cu",),
+}
+
+
+def kernel_source_hash(which: str = "codec") -> str:
+    """Hash of a kernel family's code (line comments and blank lines left out,
     so that editing a comment keeps recorded counters valid)."""
     h = hashlib.sha256()
-    for f in ("adct_codec_kernel.cuh", "adct_codec.cu", "adct_device.cuh", "adct_codec_zonal_lo.cu",
-              "adct_codec_zonal_hi.cu"):
+    for f in KERNEL_SOURCES[which]:
         with open(os.path.join(ROOT, "paper_1702_00817_gb300", "csrc", f), encoding="utf-8") as fh:
             for line in fh:
                 code = line.split("//", 1)[0].rstrip()
@@ -210,13 +216,13 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str):
+def recorded_traffic(kernel: str, which: str = "codec"):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
     the current kernel source (otherwise None)."""
     path = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
     if not os.path.exists(path):
         return None
-    cur = kernel_source_hash()
+    cur = kernel_source_hash(which)
     for line in open(path):
         parts = line.split()
         if len(parts) >= 3 and not line.startswith("#") and parts[0] == kernel and parts[1] == cur:
@@ -753,7 +759,8 @@ def run_float(args):
                 "roofline": {"bound": "hbm", "achieved": blocks * (512 + 768) / (kernel_ms / max(1, launches) * 2 / 1e3) / 1e9,
                              "peak": peak, "unit": "GB/s", "peak_kind": peak_kind,
                              "frac": blocks * (512 + 768) / (kernel_ms / max(1, launches) * 2 / 1e3) / 1e9 / peak,
-                             "kernel": "k_float_fwd + k_float_bwd (mean of the pair)", "traffic": None},
+                             "kernel": "k_float_fwd + k_float_bwd (the pair of one step)",
+                             "traffic": recorded_traffic("k_float_pair", "float")},
                 "gpu_launches": launches}
         print(json.dumps(line), flush=True)
     codec.close()
