@@ -768,6 +768,9 @@ def run_float(args):
     return 0
 
 
+SERVING_MAX_RATE = 5000  # the workload's offered rates run from 100 to 5000 req/s
+
+
 def run_serving(args):
     """Poisson stream of encode/decode requests (50/50) of sizes uniform over
     {256^2, 512^2, 1080x1920, 2160x3840, 4096^2}, 4 GB device budget; the
@@ -821,15 +824,20 @@ def run_serving(args):
         results[name] = {"rows": rows, "stats": dict(srv.stats)}
         srv.close()
     if d.rank == 0:
-        top = results["native"]["rows"][-1]
+        # headline: the highest offered rate of the workload (100-5000 req/s); the
+        # rates above it are reported as overload rows
+        rows_n = results["native"]["rows"]
+        inside = [r for r in rows_n if r["offered_req_s"] <= SERVING_MAX_RATE]
+        top = inside[-1]
         line = {"metric": METRIC, "value": top["req_s"], "unit": "req/s", "n_gpus": d.ws,
-                "steps": len(results["native"]["rows"]), "warmup": 1, "ms_per_step": None, "higher_is_better": True,
+                "steps": len(inside), "warmup": 1, "ms_per_step": None, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
                 "config": {"workload": "serving: Poisson encode/decode 50/50, sizes {256^2,512^2,1080x1920,"
                                        "2160x3840,4096^2}, 4 GB budget, on-device coefficient store; native "
                                        "scheduler (adct_server_*), Python scheduler for comparison",
-                           "seconds_per_rate": duration},
-                "serving": results["native"]["rows"], "p50_ms": top["p50_ms"], "p99_ms": top["p99_ms"],
+                           "seconds_per_rate": duration, "headline_offered_req_s": top["offered_req_s"]},
+                "serving": inside, "p50_ms": top["p50_ms"], "p99_ms": top["p99_ms"], "errors": top["errors"],
+                "overload": [r for r in rows_n if r["offered_req_s"] > SERVING_MAX_RATE],
                 "server_stats": results["native"]["stats"], "python_scheduler": results["python"]}
         print(json.dumps(line), flush=True)
     d.close()
