@@ -819,7 +819,8 @@ def run_serving(args):
             rows.append({"offered_req_s": rate, "req_s": len(ok) / wall, "p50_ms": float(np.percentile(lat, 50)),
                          "p99_ms": float(np.percentile(lat, 99)), "errors": len(reqs) - len(ok),
                          "blocks_s": px / 64 / wall, "client_late_p99_ms": float(np.percentile(late, 99)),
-                         "client_late_max_ms": float(late.max())})
+                         "client_late_max_ms": float(late.max()),
+                         "client_submit_max_ms": float(max(r.t_submitted - r.t_sent for r in reqs) * 1000.0)})
         gc.enable()
         results[name] = {"rows": rows, "stats": dict(srv.stats)}
         srv.close()

@@ -37,6 +37,7 @@ class Request:
     handle: int | None = None       # decode: store handle
     t_arrival: float = 0.0
     t_sent: float = 0.0             # poisson_run: when the client handed it to submit (>= t_arrival)
+    t_submitted: float = 0.0        # poisson_run: when submit returned
     t_admit: float = 0.0
     t_done: float = 0.0
     result: object = None           # encode: handle; decode: host uint8 [H, W]
@@ -369,6 +370,7 @@ def poisson_run(server, rate: float, n_requests: int, sizes, images_by_size, see
             pending_dec.append(r)
         r.t_sent = time.perf_counter()
         server.submit(r)
+        r.t_submitted = time.perf_counter()
         reqs.append(r)
     for r in reqs:
         r.done.wait(120)
