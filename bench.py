@@ -243,7 +243,8 @@ def make_quants(make_quant, step_table, modes):
 
 def cpu_oracle_blocks_per_s(planes, settings, target_cpu_s=10.0, cores=None):
     """Times the oracle (as it stands) on host threads over a bounded sample of
-    planes of the workload; returns (blocks/s, cores, sample description)."""
+    planes of the workload; returns (blocks/s, cores, sample description,
+    blocks/s of one thread on 8 planes run one after another)."""
     import numpy as np
 
     import oracle
@@ -272,7 +273,12 @@ def cpu_oracle_blocks_per_s(planes, settings, target_cpu_s=10.0, cores=None):
     with ThreadPoolExecutor(max_workers=cores) as ex:
         list(ex.map(lambda k: run(k, k % cores), range(count)))
     wall = time.perf_counter() - t0
-    return count * nb / wall, cores, f"{count} planes of {h}x{w} ({count * nb} blocks), settings cycled, {cores} threads"
+    t0 = time.perf_counter()
+    for k in range(8):
+        run(k, 0)
+    one = 8 * nb / (time.perf_counter() - t0)
+    return (count * nb / wall, cores, f"{count} planes of {h}x{w} ({count * nb} blocks), settings cycled, {cores} threads",
+            one)
 
 
 # ---------------------------------------------------------------- workloads
@@ -409,8 +415,9 @@ def run_roundtrip(args):
 
     cpu = None
     if not args.no_cpu and d.rank == 0 and d.ws == 1:
-        bps, cores, sample = cpu_oracle_blocks_per_s([host[k] for k in range(min(8, n))], SETTINGS)
-        cpu = {"value": bps, "unit": "blocks/s", "cores": cores, "kind": "oracle", "sample": sample}
+        bps, cores, sample, one = cpu_oracle_blocks_per_s([host[k] for k in range(min(8, n))], SETTINGS)
+        cpu = {"value": bps, "unit": "blocks/s", "cores": cores, "kind": "oracle", "sample": sample,
+               "one_thread": {"value": one, "unit": "blocks/s", "sample": "8 planes of the batch, settings cycled"}}
 
     if d.rank == 0:
         line = {
