@@ -479,7 +479,8 @@ __device__ __forceinline__ uint32_t block_step(uint8_t* __restrict__ in, uint8_t
 // NCH planar tiles: each row's channel words are interleaved in registers
 // (byte b of the span is byte (b / NCH) & 3 of channel b % NCH's word
 // (b / NCH) / 4) and written with NCH 8-byte stores, so the warp covers 256 NCH
-// contiguous bytes per row; byte by byte on the image's right edge.
+// contiguous bytes per row; on the image's right edge only the valid bytes
+// of each 8-byte part (store_prefix8).
 template <int NCH, bool EDGE>
 __device__ __forceinline__ void write_pixels_interleaved(const uint8_t* __restrict__ stage,
                                                         const PlaneDesc* __restrict__ planes, const Pos& pos,
