@@ -111,3 +111,29 @@ def test_shard_plan_is_a_balanced_partition():
     with pytest.raises(AdctError) as e:
         shard_plan([(12, 8)], 2, 0)
     assert e.value.status == _native.ADCT_ERR_SHAPE
+
+
+def test_header_compiles_as_c_and_links(lib, tmp_path):
+    """The header is plain C (C11, no CUDA headers needed) and a C program
+    links against the library and calls it; without a GPU, context creation
+    fails with a status, not a crash."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_adct.c"
+    src.write_text('#include "adct.h"\n#include <stdio.h>\n'
+                   "int main(void) {\n"
+                   "  adct_context* ctx = NULL;\n"
+                   "  adct_status st = adct_create(&ctx, 0);\n"
+                   '  printf("%s\\n", adct_status_string(st));\n'
+                   "  if (st == ADCT_OK) adct_destroy(ctx);\n"
+                   "  return 0;\n}\n")
+    libdir = os.path.dirname(_build.LIB)
+    exe = tmp_path / "use_adct"
+    subprocess.run([gcc, "-std=c11", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-L", libdir, "-ladct", "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0
+    assert out.stdout.strip().startswith("ADCT_")
