@@ -200,6 +200,7 @@ KERNEL_SOURCES = {
     "codec": ("adct_codec_kernel.cuh", "adct_codec.cu", "adct_device.cuh", "adct_codec_zonal_lo.cu",
               "adct_codec_zonal_hi.cu"),
     "float": ("adct_float.cu",),
+    "interleaved": ("adct_codec_kernel.cuh", "adct_device.cuh", "adct_codec_interleaved.cu"),
 }
 
 
@@ -609,7 +610,7 @@ def run_layout(args):
                                        f"planar, and planar {H}x{W2} with edge blocks", "l2": "inputs larger than L2"},
                 "roofline": {"bound": "hbm", "achieved": head["gbs"], "peak": peak, "unit": "GB/s",
                              "frac": head["frac"], "peak_kind": peak_kind, "kernel": "k_codec<RT_FULL, NCH=3>",
-                             "traffic": None},
+                             "traffic": recorded_traffic("k_codec_rt_inter3", "interleaved")},
                 "forms": rows, "interleaved_equals_planar": same}
         print(json.dumps(line), flush=True)
     codec.close()
