@@ -77,9 +77,24 @@ def _pix_geometry(t: torch.Tensor, interleaved: bool = False):
     raise ValueError("pixel tensors are [H, W] or [C, H, W]")
 
 
-def image_struct(im, cpb: int = 64) -> N.adct_image:
+def _check_place(t: torch.Tensor, device, what: str):
+    """device: None (no check), "cpu" (host tensors, the host pipeline) or a
+    CUDA device index (device memory on that GPU)."""
+    if device is None:
+        return
+    if device == "cpu":
+        if t.is_cuda:
+            raise ValueError(f"{what}: the host pipeline takes host tensors")
+    elif not t.is_cuda or t.device.index != device:
+        raise ValueError(f"{what} must be a CUDA tensor on cuda:{device}")
+
+
+def image_struct(im, cpb: int = 64, device=None) -> N.adct_image:
     if isinstance(im, (tuple, list)):
         im = Image(*im)
+    for t, what in ((im.src, "src"), (im.dst, "dst"), (im.coef, "coef")):
+        if t is not None:
+            _check_place(t, device, what)
     ref = im.src if im.src is not None else im.dst
     s = N.adct_image()
     if ref is not None:
@@ -110,11 +125,13 @@ def image_struct(im, cpb: int = 64) -> N.adct_image:
     return s
 
 
-def image_array(images, quant=None):
+def image_array(images, quant=None, device=None):
+    """adct_image array of `images`; device as in _check_place (the Codec
+    passes its GPU, or "cpu" for the host pipeline)."""
     cpb = coef_per_block(quant)
     arr = (N.adct_image * max(1, len(images)))()
     for k, im in enumerate(images):
-        arr[k] = image_struct(im, cpb)
+        arr[k] = image_struct(im, cpb, device)
     return arr
 
 
@@ -124,9 +141,12 @@ def _stream_handle(device: int, stream) -> ctypes.c_void_p:
     return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
 
 
-def _f32(t: torch.Tensor, name: str):
+def _f32(t: torch.Tensor, name: str, device: int | None = None, like: torch.Tensor | None = None):
     if t.dtype != torch.float32 or not t.is_contiguous() or t.dim() < 2:
         raise ValueError(f"{name} must be a contiguous float32 tensor [..., H, W]")
+    _check_place(t, device, name)
+    if like is not None and t.shape != like.shape:
+        raise ValueError(f"{name} must have the shape of x")
     H, W = t.shape[-2], t.shape[-1]
     return t.numel() // (H * W), H, W
 
@@ -169,7 +189,7 @@ class Codec:
 
     # -- integer codec ------------------------------------------------------
     def _call(self, name, images, quant=None, stream=None):
-        arr = image_array(images, quant)
+        arr = image_array(images, quant, self.device)
         args = [self.ctx, arr, len(images)]
         if quant is not None:
             args.append(ctypes.byref(quant))
@@ -189,7 +209,7 @@ class Codec:
         self._call("adct_roundtrip", images, quant, stream)
 
     def roundtrip_graph(self, images, quant, stream=None) -> bool:
-        arr = image_array(images, quant)
+        arr = image_array(images, quant, self.device)
         rep = ctypes.c_int32(0)
         st = self.lib.adct_roundtrip_graph(self.ctx, arr, len(images), ctypes.byref(quant),
                                            _stream_handle(self.device, stream), ctypes.byref(rep))
@@ -220,7 +240,7 @@ class Codec:
                 shape = table[key]["launch"]
                 self.set_launch(shape["threads_per_cta"], shape["ctas_per_sm"] or -1, shape["stage_coef"])
                 return shape, None
-        arr = image_array(images, quant)
+        arr = image_array(images, quant, self.device)
         best = N.adct_launch()
         us = ctypes.c_float(0)
         st = self.lib.adct_autotune(self.ctx, arr, len(images), ctypes.byref(quant),
@@ -248,13 +268,13 @@ class Codec:
 
     def roundtrip_host(self, images, quant, chunk_bytes: int = 32 << 20):
         """End-to-end round trip on host (ideally pinned) tensors; synchronous."""
-        arr = image_array(images, quant)
+        arr = image_array(images, quant, "cpu")
         st = self.lib.adct_roundtrip_host(self.ctx, arr, len(images), ctypes.byref(quant), int(chunk_bytes))
         N.check(st, self.ctx, "adct_roundtrip_host", lib=self.lib)
 
     def quality(self, images, quant, stream=None) -> torch.Tensor:
         """Per-plane sum of squared round-trip error (int64 tensor on the device)."""
-        arr = image_array(images)
+        arr = image_array(images, None, self.device)
         planes = sum(image_struct(im).channels for im in images)
         sse = torch.empty(max(1, planes), dtype=torch.int64, device=torch.device("cuda", self.device))
         st = self.lib.adct_quality(self.ctx, arr, len(images), ctypes.byref(quant), sse.data_ptr(),
@@ -264,7 +284,7 @@ class Codec:
 
     def quality_dct(self, images, r: int, stream=None) -> torch.Tensor:
         """Per-plane sum of squared error of the exact-DCT zonal round trip keeping r coefficients."""
-        arr = image_array(images)
+        arr = image_array(images, None, self.device)
         planes = sum(image_struct(im).channels for im in images)
         sse = torch.empty(max(1, planes), dtype=torch.int64, device=torch.device("cuda", self.device))
         st = self.lib.adct_quality_dct(self.ctx, arr, len(images), int(r), sse.data_ptr(),
@@ -294,9 +314,9 @@ class Codec:
 
     # -- float variant ------------------------------------------------------
     def forward_f32(self, x: torch.Tensor, Qsoft=None, out: torch.Tensor | None = None, stream=None):
-        planes, H, W = _f32(x, "x")
+        planes, H, W = _f32(x, "x", self.device)
         y = torch.empty_like(x) if out is None else out
-        _f32(y, "out")
+        _f32(y, "out", self.device, x)
         st = self.lib.adct_forward_f32(self.ctx, x.data_ptr(), y.data_ptr(), planes, H, W, _qsoft(Qsoft),
                                        _stream_handle(self.device, stream))
         N.check(st, self.ctx, "adct_forward_f32", lib=self.lib)
@@ -304,9 +324,10 @@ class Codec:
 
     def backward_f32(self, x: torch.Tensor, gy: torch.Tensor, Qsoft=None, out: torch.Tensor | None = None,
                      stream=None):
-        planes, H, W = _f32(x, "x")
-        _f32(gy, "gy")
+        planes, H, W = _f32(x, "x", self.device)
+        _f32(gy, "gy", self.device, x)
         gx = torch.empty_like(x) if out is None else out
+        _f32(gx, "out", self.device, x)
         st = self.lib.adct_backward_f32(self.ctx, x.data_ptr(), gy.data_ptr(), gx.data_ptr(), planes, H, W,
                                         _qsoft(Qsoft), _stream_handle(self.device, stream))
         N.check(st, self.ctx, "adct_backward_f32", lib=self.lib)

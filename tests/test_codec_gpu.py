@@ -442,3 +442,13 @@ def test_autotune_cache_file(codec, tmp_path):
     for x, im in zip(imgs, ims):
         assert np.array_equal(im.dst.cpu().numpy(), oracle.roundtrip(x, oracle.MODE_STEP, inputs.step_table(4))[1])
     codec.set_launch(before["threads_per_cta"], before["ctas_per_sm"] or -1, before["stage_coef"])
+
+
+def test_binding_refuses_host_tensors_for_device_calls(codec):
+    src = torch.zeros((16, 16), dtype=torch.uint8)
+    with pytest.raises(ValueError):
+        codec.roundtrip([Image(src, torch.zeros_like(src), None)], make_quant(ADCT_Q_STEP, inputs.step_table(4)))
+    dev_src = src.to(DEV)
+    with pytest.raises(ValueError):
+        codec.roundtrip_host([Image(dev_src, torch.zeros_like(dev_src), None)],
+                             make_quant(ADCT_Q_STEP, inputs.step_table(4)))

@@ -71,3 +71,13 @@ def test_float_argument_errors(codec):
         codec.forward_f32(x)
     with pytest.raises(AdctError):
         codec.forward_f32(torch.zeros((1, 8, 8), device=DEV), np.zeros(64))
+
+
+def test_float_binding_refuses_mismatched_or_host_tensors(codec):
+    x = torch.zeros((2, 8, 16), device=DEV)
+    with pytest.raises(ValueError):
+        codec.backward_f32(x, torch.zeros((1, 8, 16), device=DEV))  # gy smaller than x
+    with pytest.raises(ValueError):
+        codec.forward_f32(x, out=torch.zeros((1, 8, 16), device=DEV))
+    with pytest.raises(ValueError):
+        codec.forward_f32(torch.zeros((2, 8, 16)))  # host tensor
