@@ -421,6 +421,8 @@ class NativeServer:
         with self._lock:
             if req.kind == "encode":
                 px = req.pixels
+                if px.is_cuda or px.dtype != torch.uint8 or px.dim() != 2 or px.stride(1) != 1:
+                    raise ValueError("NativeServer encodes host uint8 [H, W] tensors with unit column stride")
                 H, W = px.shape
                 st = self.lib.adct_server_encode(self._srv, px.data_ptr(), W, H, px.stride(0), t_sub, ct.byref(rid))
             else:
