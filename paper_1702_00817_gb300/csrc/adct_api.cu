@@ -1164,12 +1164,18 @@ thread_local int64_t g_adds = 0;
 struct Counted {
   int64_t v;
 };
-inline Counted operator+(Counted a, Counted b) {
+// Host and device so that the butterfly templates (host-device functions)
+// instantiate cleanly for it; only host calls exist, and only they count.
+__host__ __device__ inline Counted operator+(Counted a, Counted b) {
+#ifndef __CUDA_ARCH__
   ++g_adds;
+#endif
   return Counted{a.v + b.v};
 }
-inline Counted operator-(Counted a, Counted b) {
+__host__ __device__ inline Counted operator-(Counted a, Counted b) {
+#ifndef __CUDA_ARCH__
   ++g_adds;
+#endif
   return Counted{a.v - b.v};
 }
 }  // namespace
