@@ -1125,10 +1125,12 @@ extern "C" adct_status adct_shard_plan(const adct_image* imgs, int32_t n, int32_
   std::vector<int64_t> blocks((size_t)n);
   for (int32_t m = 0; m < n; ++m) {
     const adct_image& im = imgs[m];
-    if (im.width <= 0 || im.height <= 0 || im.width % 8 || im.height % 8 || im.width > 65536 || im.height > 65536 ||
-        im.channels < 1)
+    const bool inter = im.layout == ADCT_LAYOUT_INTERLEAVED;
+    if (im.width <= 0 || im.height <= 0 || im.width > 65536 || im.height > 65536 || im.channels < 1 ||
+        (im.layout != ADCT_LAYOUT_PLANAR && !inter) || (inter && im.channels != 3 && im.channels != 4))
       return ADCT_ERR_SHAPE;
-    blocks[m] = (int64_t)(im.width / 8) * (im.height / 8) * im.channels;
+    // any side: edge blocks count as whole blocks (ceil(side / 8) per side)
+    blocks[m] = (int64_t)((im.width + 7) / 8) * ((im.height + 7) / 8) * im.channels;
   }
   std::vector<int32_t> order((size_t)n);
   for (int32_t m = 0; m < n; ++m) order[m] = m;

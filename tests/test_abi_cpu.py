@@ -108,9 +108,13 @@ def test_shard_plan_is_a_balanced_partition():
         with pytest.raises(AdctError) as e:
             shard_plan(sizes, *bad)
         assert e.value.status == _native.ADCT_ERR_INVALID_ARG
-    with pytest.raises(AdctError) as e:
-        shard_plan([(12, 8)], 2, 0)
-    assert e.value.status == _native.ADCT_ERR_SHAPE
+    for bad_shape in ((0, 8), (8, 65544), (0, 8, 8)):
+        with pytest.raises(AdctError) as e:
+            shard_plan([bad_shape], 2, 0)
+        assert e.value.status == _native.ADCT_ERR_SHAPE
+    # any side: edge blocks count whole, ceil(side / 8) per side
+    assert shard_plan([(12, 8), (9, 17)], 1, 0) == ([0, 1], 2 + 2 * 3)
+    assert shard_plan([(1, 1)] * 3, 2, 1) == ([1], 2)
 
 
 def test_header_compiles_as_c_and_links(lib, tmp_path):
