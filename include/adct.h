@@ -265,7 +265,9 @@ adct_status adct_autotune(adct_context* ctx, const adct_image* imgs, int32_t n, 
  * device, transformed with adct_roundtrip and copied back, with chunks
  * pipelined over the context's copy/compute streams.  Device staging is owned
  * by ctx and grows to the largest chunk.  Synchronous: returns when every
- * output is in host memory.
+ * output is in host memory.  Planar images with sides that are multiples of 8
+ * only: ADCT_ERR_UNSUPPORTED for an interleaved image, ADCT_ERR_SHAPE for
+ * other sides (the device entry points take any size).
  */
 adct_status adct_roundtrip_host(adct_context* ctx, const adct_image* host_imgs, int32_t n, const adct_quant* quant,
                                 int64_t chunk_bytes);
@@ -357,7 +359,8 @@ adct_status adct_roundtrip_noalloc(const adct_image* imgs, int32_t n, const adct
  * packs its admissions into one encode launch and one decode launch on the next
  * of its streams, so batches overlap on the device.  Results are identical to
  * adct_roundtrip / adct_inverse on the same inputs.
- *   encode: host pixels (width x height uint8, rows pitch bytes apart) are
+ *   encode: host pixels (width x height uint8, rows pitch bytes apart; width
+ *           and height multiples of 8 up to 65536, else ADCT_ERR_SHAPE) are
  *           copied in, forward-transformed and quantised; the coefficients stay
  *           in the store under the handle reported by the completion (2r bytes
  *           per block with ADCT_Q_ZONAL_ZZ, 128 otherwise).
