@@ -141,3 +141,26 @@ def test_header_compiles_as_c_and_links(lib, tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert out.returncode == 0
     assert out.stdout.strip().startswith("ADCT_")
+
+
+def test_shard_plan_properties_on_random_batches():
+    """Random batches (hypothesis): every rank's list is sorted, the lists
+    partition the batch, the reported maximum is the largest rank load, and
+    the load spread stays within the largest image (greedy list scheduling)."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+    from paper_1702_00817_gb300.codec import shard_plan
+
+    @hyp.settings(max_examples=60, deadline=None)
+    @hyp.given(st.lists(st.tuples(st.integers(1, 4), st.integers(1, 600), st.integers(1, 600)), max_size=40),
+               st.integers(1, 9))
+    def check(shapes, world):
+        blocks = [c * ((h + 7) // 8) * ((w + 7) // 8) for c, h, w in shapes]
+        plans = [shard_plan(shapes, world, r) for r in range(world)]
+        assert sorted(i for p, _ in plans for i in p) == list(range(len(shapes)))
+        loads = [sum(blocks[i] for i in p) for p, _ in plans]
+        assert all(p == sorted(p) and mx == max(loads, default=0) for (p, mx) in plans)
+        if blocks:
+            assert max(loads) - min(loads) <= max(blocks)
+
+    check()
