@@ -251,6 +251,71 @@ def test_soft_quantiser_fixed_points():
     assert np.allclose(z, 0.0)
 
 
+# Closed forms of the soft quantiser z(y) = y - (Q/2pi) sin(2 pi y / Q) and
+# its derivative 1 - cos(2 pi y / Q) at y = f Q, written out by hand.
+_SOFT_POINTS = [  # (f, z / Q, dz/dy)
+    (0.25, 0.25 - 1 / (2 * math.pi), 1.0),
+    (0.5, 0.5, 2.0),
+    (0.75, 0.75 + 1 / (2 * math.pi), 1.0),
+    (1.0, 1.0, 0.0),
+    (-0.25, -0.25 + 1 / (2 * math.pi), 1.0),
+]
+
+
+def _orthonormal_rows():
+    # C^ = D T from the printed factors and the printed D (Sec. 2), not from the oracle
+    d = 1.0 / np.sqrt(np.array(paper_numbers()["inv_d2"][0]))
+    return d[:, None] * _factor_T().astype(np.float64)
+
+
+@pytest.mark.parametrize("Qv", [1.0, 3.0, 0.5, 37.0])
+def test_soft_quantiser_constant_block_closed_form(Qv):
+    # Sec. 2: T 1 = 8 e0 and d_0^2 = 1/8, so a constant block x = c gives
+    # y_00 = 64 c / 8 = 8 c and y_ij = 0 elsewhere.  Choosing c = f Q / 8 puts
+    # y_00 at f Q, where z_00 and dz/dy have the closed forms above; every
+    # other z_ij is 0.  A dropped D, a sin(pi y / Q), a Q/pi factor or a sign
+    # error in the soft term moves z_00 off these values.
+    Q = np.full(64, Qv)
+    for f, zq, dzdy in _SOFT_POINTS:
+        x = np.full((1, 8, 8), f * Qv / 8.0)
+        z, y = oracle.forward_f64(x, Q, want_y=True)
+        assert abs(y[0, 0, 0] - f * Qv) <= 1e-12 * max(1.0, Qv)
+        assert abs(z[0, 0, 0] - zq * Qv) <= 1e-12 * max(1.0, Qv)
+        zz = z.copy()
+        zz[0, 0, 0] = 0.0
+        assert np.abs(zz).max() <= 1e-12 * max(1.0, Qv)
+        # adjoint with g_z = e_00: g_x = C^T (e_00 dz/dy) C = dz/dy / 8 everywhere
+        gz = np.zeros((1, 8, 8))
+        gz[0, 0, 0] = 1.0
+        gx = oracle.backward_f64(x, gz, Q)
+        assert np.abs(gx - dzdy / 8.0).max() <= 1e-12
+
+
+@pytest.mark.parametrize("i,j", [(0, 1), (2, 5), (3, 3), (7, 4), (6, 0)])
+def test_soft_quantiser_single_coefficient_closed_form(i, j):
+    # A basis block x = A C^[i]^T C^[j] (C^ = D T orthonormal, Sec. 2) has the
+    # single coefficient y_ij = A.  With a different step at every position the
+    # soft term must use Q_ij (a transposed table index fails); the adjoint of
+    # g_z = e_ij is dz/dy * C^[i]^T C^[j].
+    C = _orthonormal_rows()
+    Q = 1.0 + 0.25 * np.arange(64)  # Q_ij = 1 + (8 i + j) / 4, no symmetry
+    Qij = Q[8 * i + j]
+    basis = np.outer(C[i], C[j])
+    for f, zq, dzdy in _SOFT_POINTS:
+        x = (f * Qij * basis)[None]
+        z, y = oracle.forward_f64(x, Q, want_y=True)
+        expect_y = np.zeros((8, 8))
+        expect_y[i, j] = f * Qij
+        assert np.abs(y[0] - expect_y).max() <= 1e-12 * Qij
+        expect_z = np.zeros((8, 8))
+        expect_z[i, j] = zq * Qij
+        assert np.abs(z[0] - expect_z).max() <= 1e-12 * Qij
+        gz = np.zeros((1, 8, 8))
+        gz[0, i, j] = 1.0
+        gx = oracle.backward_f64(x, gz, Q)
+        assert np.abs(gx[0] - dzdy * basis).max() <= 1e-12
+
+
 @pytest.mark.parametrize("Qkind", ["ones", "step1"])
 def test_float_adjoint_matches_central_finite_differences(Qkind):
     # FP64 central differences, h = 1e-3, relative error < 1e-4.
