@@ -333,18 +333,24 @@ adct_status adct_kernel_time(adct_context* ctx, double* total_ms, int64_t* launc
  * Same arguments and results as adct_roundtrip (bit for bit), but no context:
  * the per-call plane descriptor table lives in a fixed device array inside the
  * library, sized for ADCT_NOALLOC_MAX_PLANES planes (a plane is one channel of
- * one image), about 57 KB that every GPU which loads the library keeps until
- * the process exits.  A batch with more planes returns ADCT_ERR_TOO_LARGE and
- * launches nothing.  It runs on the calling thread's current CUDA device; the
- * first call on a device looks up that array's device address, so make the
- * first call before any stream capture.  The table is copied from host memory
- * on `stream` (a copy from pageable memory, so the call waits for the work
- * already queued on that stream).  Every call shares the one array and it
- * keeps the last call's table; nothing in it needs clearing, because each call
- * writes the whole table it reads.  Calls whose work overlaps on the GPU (on
- * different streams, or from different host threads) race on the array:
+ * one image; an interleaved image counts as one): 73,776 bytes (1024 64-byte
+ * descriptors plus 1030 8-byte block-count prefixes) that every GPU which
+ * loads the library keeps until the process exits.  A batch with more planes
+ * returns ADCT_ERR_TOO_LARGE and launches nothing.  It runs on the calling
+ * thread's current CUDA device; the first call on a device looks up that
+ * array's device address, so make the first call before any stream capture.
+ * The table is built in one host buffer of the same size inside the library
+ * (not on the caller's stack, so threads with small stacks can call it),
+ * under a lock that calls from several host threads take in turn, and copied on
+ * `stream` (a copy from pageable memory, so the call waits for the work
+ * already queued on that stream).  Every call shares the one device array and
+ * it keeps the last call's table; nothing in it needs clearing, because each
+ * call writes the whole table it reads.  Calls whose work overlaps on the GPU
+ * (on different streams, or from different host threads) race on the array:
  * serialise them on one stream.  Argument errors return the same codes as
- * adct_roundtrip (there is no context, so no adct_last_error message).
+ * adct_roundtrip (there is no context, so no adct_last_error message, and in
+ * the checked build the kernels' bounds checks have no fault word to report
+ * to on this path: a tile outside its plane is skipped without a report).
  */
 #define ADCT_NOALLOC_MAX_PLANES 1024
 adct_status adct_roundtrip_noalloc(const adct_image* imgs, int32_t n, const adct_quant* quant, adct_stream_t stream);

@@ -1233,6 +1233,16 @@ struct NoAllocDevice {
 NoAllocDevice g_noalloc_devices[kNoAllocMaxDevices];
 std::mutex g_noalloc_mutex;
 
+// Host copy of the table, built call by call in this one buffer (guarded by
+// g_noalloc_table_mutex) and copied into g_noalloc_scratch: the same layout.
+struct NoAllocTable {
+  PlaneDesc planes[kNoAllocPlanes];
+  int64_t starts[kNoAllocPlanes + kGroups];
+};
+static_assert(sizeof(NoAllocTable) == kNoAllocBytes, "host table layout matches the device array");
+NoAllocTable g_noalloc_table;
+std::mutex g_noalloc_table_mutex;
+
 adct_status noalloc_device(int dev, void** scratch, int* sm_count) {
   if (dev < 0 || dev >= kNoAllocMaxDevices) return ADCT_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
@@ -1269,20 +1279,15 @@ extern "C" adct_status adct_roundtrip_noalloc(const adct_image* imgs, int32_t n,
   if (n == 0) return ADCT_OK;
   const bool want_coef = imgs[0].coef != nullptr, want_dst = imgs[0].dst != nullptr;
   if (!want_coef && !want_dst) return ADCT_ERR_INVALID_ARG;
-  CodecLaunch cl{};
+  CodecLaunch cl{};  // cl.fault stays null: no context, so a checked build reports no bounds faults here
   cl.kind = (want_coef && want_dst) ? K_RT_FULL : (want_dst ? K_RT_PIX : K_RT_COEF);
   adct_status st = build_quant(nullptr, quant, true, cl.qp, cl.evenq);
   if (st != ADCT_OK) return st;
   cl.qmode = quant->mode;
 
-  // Descriptor tables built on the stack: nothing is allocated.  The groups
-  // (pixel layout classes) are laid out one after the other, all planes
-  // first, then each group's flat-index prefix.
-  struct {
-    PlaneDesc planes[kNoAllocPlanes];
-    int64_t starts[kNoAllocPlanes + kGroups];
-  } table;
-  static_assert(sizeof(table) == kNoAllocBytes, "table layout matches the device array");
+  // Validation first (nothing shared is touched): the plane count is checked
+  // against the table's capacity before it is added, so no channel count,
+  // however large, can overflow the sum.
   const int need = NEED_SRC | (want_coef ? NEED_COEF : 0) | (want_dst ? NEED_DST : 0);
   const int32_t cpb = coef_per_block(quant);
   int32_t planes_total = 0;
@@ -1292,9 +1297,18 @@ extern "C" adct_status adct_roundtrip_noalloc(const adct_image* imgs, int32_t n,
     const char* why = "";
     st = check_image(im, need, false, &why);
     if (st != ADCT_OK) return st;
-    planes_total += im.layout == ADCT_LAYOUT_INTERLEAVED ? 1 : im.channels;
-    if (planes_total > kNoAllocPlanes) return ADCT_ERR_TOO_LARGE;
+    const int32_t add = im.layout == ADCT_LAYOUT_INTERLEAVED ? 1 : im.channels;
+    if (add > kNoAllocPlanes - planes_total) return ADCT_ERR_TOO_LARGE;
+    planes_total += add;
   }
+
+  // The descriptor tables are built in the library's one host buffer (not on
+  // the caller's stack, which may be small on threads that a host application
+  // owns), under a lock held until the copy to the device has been issued.
+  std::lock_guard<std::mutex> table_lock(g_noalloc_table_mutex);
+  NoAllocTable& table = g_noalloc_table;
+  // The groups (pixel layout classes) are laid out one after the other, all
+  // planes first, then each group's flat-index prefix.
   int32_t np = 0, gfirst[kGroups], gcount[kGroups];
   for (int g = 0; g < kGroups; ++g) {  // one pass per group keeps each group's descriptors together
     gfirst[g] = np;

@@ -164,3 +164,63 @@ def test_shard_plan_properties_on_random_batches():
             assert max(loads) - min(loads) <= max(blocks)
 
     check()
+
+
+def _fake_planar(channels, side=8):
+    """An adct_image with aligned placeholder pointers; only validation reads it."""
+    im = _native.adct_image()
+    im.src, im.dst = 0x10000, 0x20000
+    im.width = im.height = side
+    im.channels = channels
+    im.layout = _native.ADCT_LAYOUT_PLANAR
+    im.pitch, im.plane_stride = side, side * side
+    return im
+
+
+def _noalloc_args(images):
+    import ctypes
+    from paper_1702_00817_gb300.codec import ADCT_Q_STEP, make_quant
+    arr = (_native.adct_image * len(images))(*images)
+    return arr, make_quant(ADCT_Q_STEP, np.full(64, 3))
+
+
+def test_noalloc_plane_count_cannot_overflow(lib):
+    # A channel count near INT32_MAX after other planes must be refused as too
+    # large, not wrap the running plane count past the table's limit.  Checked
+    # on the host before any device work, so no GPU is involved.
+    import ctypes
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("placeholder pointers: host-only check")
+    for first, second in ((1, 2 ** 31 - 1), (1023, 2), (1000, 2 ** 31 - 1000)):
+        arr, q = _noalloc_args([_fake_planar(first), _fake_planar(second)])
+        assert lib.adct_roundtrip_noalloc(arr, 2, ctypes.byref(q), None) == _native.ADCT_ERR_TOO_LARGE
+
+
+def test_noalloc_table_fits_a_small_thread_stack(lib):
+    # The 72 KiB descriptor table is built in a library buffer, not on the
+    # caller's stack: a full 1024-plane batch from a thread with a 64 KiB stack
+    # gets through validation and table building to the device lookup (which
+    # fails here, with no GPU) instead of overflowing the stack.
+    import ctypes
+    import threading
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("placeholder pointers: host-only check")
+    arr, q = _noalloc_args([_fake_planar(4) for _ in range(256)])
+    out = []
+    old = None
+    for size in (65536, 131072):  # 128 KiB where that is the platform's minimum (aarch64, 64 KiB pages)
+        try:
+            old = threading.stack_size(size)
+            break
+        except ValueError:
+            continue
+    assert old is not None
+    try:
+        t = threading.Thread(target=lambda: out.append(lib.adct_roundtrip_noalloc(arr, 256, ctypes.byref(q), None)))
+        t.start()
+        t.join()
+    finally:
+        threading.stack_size(old)
+    assert out == [_native.ADCT_ERR_CUDA]
