@@ -8,9 +8,15 @@ reconstruct) in ONE launch through the C ABI.  Steps cycle through the eight
 quantiser settings: step tables Q_ij = 1 + floor(s (1 + i + j)) for s in
 {1, 4, 16} and zonal retention r in {1, 6, 10, 16, 64}.
 
-Prints one JSON line (rank 0).  Other workloads (--workload ragged | float |
-serving | quality | packed | layout) print their own lines.  --impl reference times the CPU oracle on the
-host cores instead.
+Prints one JSON line (rank 0).  Its value is the uniform round trip; after
+that timed region the line also measures, each on its own and bounded, the
+workload's other configurations: "ragged" (1000 three-channel images of
+ragged sizes per GPU: graph-captured one launch, eager one launch, per-image
+launch loop, outputs compared), "float" (forward + adjoint of 64 x 3 x
+512x512 float32) and "serving" (Poisson encode/decode stream at 5000 req/s
+offered: req/s, p50/p99, errors).  Other workloads (--workload ragged | float
+| serving | quality | packed | layout) print their own lines with more
+detail.  --impl reference times the CPU oracle on the host cores instead.
 """
 from __future__ import annotations
 
@@ -44,6 +50,8 @@ def parse():
     p.add_argument("--workload", choices=["roundtrip", "ragged", "float", "serving", "quality", "packed", "layout"], default="roundtrip")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-configs", action="store_true",
+                   help="default workload: leave out the ragged, float and serving sub-objects")
     p.add_argument("--images", type=int, default=N_IMG)
     p.add_argument("--r", type=int, nargs="*", default=[1, 6, 10, 16, 25, 64],
                    help="packed workload: zonal r values to sweep")
@@ -414,6 +422,21 @@ def run_roundtrip(args):
                "timing": f"median of {reps} windows of {esteps} steps", "windows": rates,
                "api": "adct_roundtrip_host (pinned host buffers)"}
 
+    # The other configurations of the workload, each measured on its own
+    # after the round trip's timed region (bounded: about 15 s together).
+    extra = {}
+    if not args.no_configs:
+        del src, dst, coef, images, arr
+        torch.cuda.empty_cache()
+        extra["ragged"] = measure_ragged(d, dev, steps=10, warmup=3, autotune_reps=2)
+        extra["float"] = measure_float(d, dev, steps=20, warmup=3)
+        srv = measure_serving(dev, (SERVING_MAX_RATE,))
+        row = srv["native"]["rows"][0]
+        extra["serving"] = {"offered_req_s": row["offered_req_s"], "req_s": row["req_s"], "p50_ms": row["p50_ms"],
+                            "p99_ms": row["p99_ms"], "errors": row["errors"], "requests": row["requests"],
+                            "blocks_s": row["blocks_s"], "client_late_p99_ms": row["client_late_p99_ms"],
+                            "seconds": 1.5, "workload": SERVING_WORKLOAD + f" (per GPU, rank 0 reported)"}
+
     cpu = None
     if not args.no_cpu and d.rank == 0 and d.ws == 1:
         bps, cores, sample, one = cpu_oracle_blocks_per_s([host[k] for k in range(min(8, n))], SETTINGS)
@@ -439,6 +462,7 @@ def run_roundtrip(args):
                          "algorithmic_bytes_per_launch": blocks * BYTES_PER_BLOCK, "kernel_ms": kern_avg_ms},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": sampler.summary(),
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
     codec.close()
     d.close()
@@ -631,22 +655,22 @@ def _event_time(fn, steps, stream):
     return e0.elapsed_time(e1) / 1000.0
 
 
-def run_ragged(args):
-    """Ragged batch (1000 three-channel images, sides log-uniform over 64..4096):
-    one graph-captured launch vs the same launch eager vs one launch per image."""
+RAGGED_IMAGES = 1000  # per GPU: 3-channel images, sides 8 round(2^U[6,12] / 8)
+
+
+def measure_ragged(d, dev, steps, warmup, autotune_reps=3):
+    """Ragged batch of RAGGED_IMAGES three-channel images per GPU (sides
+    log-uniform over 64..4096), step s = 4: one graph-captured launch, the
+    same launch eager, and one launch per image, each timed with CUDA events
+    over `steps` steps; outputs of the forms compared on sampled images.
+    Returns the whole-job figures (blocks of every rank / slowest rank)."""
     import torch
 
-    from paper_1702_00817_gb300 import _build, inputs
+    from paper_1702_00817_gb300 import inputs
     from paper_1702_00817_gb300.codec import ADCT_Q_STEP, Codec, Image, image_array, make_quant, shard_plan
-    d = Dist()
-    dev = torch.device("cuda", d.local)
-    torch.cuda.set_device(dev)
-    if d.rank == 0:  # one build per node: the other ranks wait, then load it
-        _build.build()
-    d.barrier()
-    # one ragged batch of 1000 images per GPU, sharded over the ranks by the
-    # library's balanced plan (each rank computes it alone: no exchange)
-    n_global = 1000 * d.ws
+    # one ragged batch per GPU, sharded over the ranks by the library's
+    # balanced plan (each rank computes it alone: no exchange)
+    n_global = RAGGED_IMAGES * d.ws
     sizes_all = inputs.ragged_sizes(n_global, seed=inputs.BASE_SEED)
     mine, max_blocks = shard_plan([(3, h, w) for h, w in sizes_all], d.ws, d.rank)
     n = len(mine)
@@ -675,11 +699,10 @@ def run_ragged(args):
         for a in singles:
             assert lib.adct_roundtrip(ctx, a, 1, ctypes.byref(q), sh) == 0
 
-    best, best_us = codec.autotune(images, q, reps=3)
+    best, best_us = codec.autotune(images, q, reps=autotune_reps)
     for fn in (graph, eager, loop):
-        for i in range(max(3, args.warmup)):
+        for i in range(max(3, warmup)):
             fn(i)
-    steps = max(1, min(args.steps, 50))
     codec.kernel_time()
     codec.kernel_timing(True)
     d.barrier()
@@ -689,50 +712,81 @@ def run_ragged(args):
     t_loop = d.max(_event_time(loop, steps, stream))
     codec.kernel_timing(False)
     # outputs of the three forms must agree bit for bit on a sample
-    out_graph = [dsts[k].clone() for k in (0, n // 2, n - 1)]
+    picks = (0, n // 2, n - 1)
+    graph(0)
+    torch.cuda.synchronize()
+    out_graph = [dsts[k].clone() for k in picks]
+    q_graph = [coefs[k].clone() for k in picks]
+    loop(0)
+    torch.cuda.synchronize()
+    same_loop = all(torch.equal(a, dsts[k]) and torch.equal(c, coefs[k]) for a, c, k in zip(out_graph, q_graph, picks))
     eager(0)
     torch.cuda.synchronize()
-    same = all(torch.equal(a, dsts[k]) for a, k in zip(out_graph, (0, n // 2, n - 1)))
+    same = same_loop and all(torch.equal(a, dsts[k]) and torch.equal(c, coefs[k])
+                             for a, c, k in zip(out_graph, q_graph, picks))
     peak, peak_kind = measured_peaks()
     total = d.sum(blocks * steps)
-    value = total / t_graph
-    if d.rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": d.ws, "steps": steps,
-                "warmup": max(3, args.warmup), "ms_per_step": 1000 * t_graph / steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-                "config": {"workload": f"ragged batch {n_global} x 3-channel u8, sides 8*round(2^U[6,12]/8), "
-                                       f"step s=4, one graph-captured launch per step per GPU",
-                           "blocks_per_gpu": blocks, "max_blocks_per_gpu": max_blocks,
-                           "parallelism": f"dp{d.ws} (images sharded by adct_shard_plan, no collective)",
-                           "l2": "inputs larger than L2", "autotuned_launch": best, "autotune_us": best_us},
-                "forms": {"graph_one_launch_blocks_s": value, "eager_one_launch_blocks_s": total / t_eager,
-                          "per_image_loop_blocks_s": total / t_loop, "graph_vs_loop": t_loop / t_graph,
-                          "outputs_identical": bool(same)},
-                "gbs": value * BYTES_PER_BLOCK / 1e9, "hbm_frac": value * BYTES_PER_BLOCK / 1e9 / peak,
-                "roofline": {"bound": "hbm", "achieved": blocks * BYTES_PER_BLOCK / (kernel_ms / max(1, launches) / 1e3) / 1e9,
-                             "peak": peak, "unit": "GB/s", "peak_kind": peak_kind,
-                             "frac": blocks * BYTES_PER_BLOCK / (kernel_ms / max(1, launches) / 1e3) / 1e9 / peak,
-                             "kernel": "graph (descriptor upload + k_codec<RT_FULL>)", "traffic": None},
-                "gpu_launches": launches}
-        print(json.dumps(line), flush=True)
+    kern_ms = kernel_ms / max(1, launches)
+    achieved = blocks * BYTES_PER_BLOCK / (kern_ms / 1e3) / 1e9
+    out = {"blocks_s": total / t_graph, "steps": steps, "ms_per_step": 1000 * t_graph / steps,
+           "config": {"workload": f"ragged batch {n_global} x 3-channel u8, sides 8*round(2^U[6,12]/8), "
+                                  f"step s=4, one graph-captured launch per step per GPU",
+                      "blocks_per_gpu": blocks, "max_blocks_per_gpu": max_blocks,
+                      "parallelism": f"dp{d.ws} (images sharded by adct_shard_plan, no collective)",
+                      "l2": f"inputs larger than L2 ({blocks * BYTES_PER_BLOCK / 1e9:.1f} GB touched per step)",
+                      "autotuned_launch": best, "autotune_us": best_us},
+           "forms": {"graph_one_launch_blocks_s": total / t_graph, "eager_one_launch_blocks_s": total / t_eager,
+                     "per_image_loop_blocks_s": total / t_loop, "graph_vs_loop": t_loop / t_graph,
+                     "eager_vs_loop": t_loop / t_eager, "outputs_identical": bool(same)},
+           "gbs": total / t_graph * BYTES_PER_BLOCK / 1e9,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "peak_kind": f"{peak_kind} (copy, burst)", "frac": achieved / peak,
+                        "kernel": "k_codec<RT_FULL> (graph replay, kernel only)",
+                        "traffic": recorded_traffic("k_codec_rt_ragged"),
+                        "algorithmic_bytes_per_launch": blocks * BYTES_PER_BLOCK, "kernel_ms": kern_ms},
+           "gpu_launches": launches}
     codec.close()
-    d.close()
-    return 0
+    del srcs, dsts, coefs, images
+    torch.cuda.empty_cache()
+    return out
 
 
-def run_float(args):
-    """Float32 forward (D T x T^T D + soft quantiser) and adjoint on 64 x 3 x 512 x 512."""
-    import numpy as np
+def run_ragged(args):
+    """Ragged batch: one graph-captured launch vs the same launch eager vs one launch per image."""
     import torch
 
-    from paper_1702_00817_gb300 import _build, inputs
-    from paper_1702_00817_gb300.codec import Codec
+    from paper_1702_00817_gb300 import _build
     d = Dist()
     dev = torch.device("cuda", d.local)
     torch.cuda.set_device(dev)
     if d.rank == 0:  # one build per node: the other ranks wait, then load it
         _build.build()
     d.barrier()
+    r = measure_ragged(d, dev, max(1, min(args.steps, 50)), args.warmup)
+    if d.rank == 0:
+        line = {"metric": METRIC, "value": r["blocks_s"], "unit": "blocks/s", "n_gpus": d.ws, "steps": r["steps"],
+                "warmup": max(3, args.warmup), "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": r["config"], "forms": r["forms"], "gbs": r["gbs"],
+                "hbm_frac": r["gbs"] / measured_peaks()[0], "roofline": r["roofline"],
+                "gpu_launches": r["gpu_launches"]}
+        print(json.dumps(line), flush=True)
+    d.close()
+    return 0
+
+
+FLOAT_BYTES_PER_BLOCK = 512 + 768  # forward: x in, y out; adjoint: x and gy in, gx out (float32)
+
+
+def measure_float(d, dev, steps, warmup):
+    """Float32 forward (D T x T^T D + soft quantiser, Q = 1) and adjoint on
+    64 x 3 x 512 x 512 N(0,1) per GPU, `steps` forward + adjoint pairs timed
+    with CUDA events; whole-job figures."""
+    import numpy as np
+    import torch
+
+    from paper_1702_00817_gb300 import inputs
+    from paper_1702_00817_gb300.codec import Codec
     x = torch.from_numpy(inputs.normal_batch((64, 3, 512, 512), seed=inputs.BASE_SEED + d.rank)).to(dev)
     gy = torch.from_numpy(inputs.normal_batch((64, 3, 512, 512), seed=inputs.BASE_SEED + 1 + d.rank)).to(dev)
     y = torch.empty_like(x)
@@ -745,33 +799,53 @@ def run_float(args):
         codec.forward_f32(x, Q, out=y)
         codec.backward_f32(x, gy, Q, out=gx)
 
-    for i in range(max(3, args.warmup)):
+    for i in range(max(3, warmup)):
         step(i)
     stream = torch.cuda.current_stream(dev)
     codec.kernel_time()
     codec.kernel_timing(True)
     d.barrier()
-    t = d.max(_event_time(step, args.steps, stream))
+    t = d.max(_event_time(step, steps, stream))
     kernel_ms, launches = codec.kernel_time()
     codec.kernel_timing(False)
-    peak, peak_kind = measured_peaks()
-    total = d.sum(blocks * args.steps)
-    value = total / t
-    if d.rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": d.ws, "steps": args.steps,
-                "warmup": max(3, args.warmup), "ms_per_step": 1000 * t / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic N(0,1)",
-                "config": {"workload": "float32 64x3x512x512: forward D T x T^T D + soft quantiser (Q=1), "
-                                       "then the adjoint kernel", "l2": "inputs larger than L2 (201 MB each)"},
-                "gbs": value * (512 + 768) / 1e9, "hbm_frac": value * (512 + 768) / 1e9 / peak,
-                "roofline": {"bound": "hbm", "achieved": blocks * (512 + 768) / (kernel_ms / max(1, launches) * 2 / 1e3) / 1e9,
-                             "peak": peak, "unit": "GB/s", "peak_kind": peak_kind,
-                             "frac": blocks * (512 + 768) / (kernel_ms / max(1, launches) * 2 / 1e3) / 1e9 / peak,
-                             "kernel": "k_float_fwd + k_float_bwd (the pair of one step)",
-                             "traffic": recorded_traffic("k_float_pair", "float")},
-                "gpu_launches": launches}
-        print(json.dumps(line), flush=True)
     codec.close()
+    peak, peak_kind = measured_peaks()
+    total = d.sum(blocks * steps)
+    pair_ms = kernel_ms / max(1, launches) * 2
+    achieved = blocks * FLOAT_BYTES_PER_BLOCK / (pair_ms / 1e3) / 1e9
+    del x, gy, y, gx
+    torch.cuda.empty_cache()
+    return {"blocks_s": total / t, "steps": steps, "ms_per_step": 1000 * t / steps,
+            "config": {"workload": "float32 64x3x512x512 N(0,1): forward D T x T^T D + soft quantiser (Q=1), "
+                                   "then the adjoint kernel", "l2": "inputs larger than L2 (201 MB each)"},
+            "gbs": total / t * FLOAT_BYTES_PER_BLOCK / 1e9,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "peak_kind": f"{peak_kind} (copy, burst)", "frac": achieved / peak,
+                         "kernel": "k_float_fwd + k_float_bwd (the pair of one step)",
+                         "traffic": recorded_traffic("k_float_pair", "float"),
+                         "algorithmic_bytes_per_launch": blocks * FLOAT_BYTES_PER_BLOCK, "kernel_ms": pair_ms},
+            "gpu_launches": launches}
+
+
+def run_float(args):
+    """Float32 forward (D T x T^T D + soft quantiser) and adjoint on 64 x 3 x 512 x 512."""
+    import torch
+
+    from paper_1702_00817_gb300 import _build
+    d = Dist()
+    dev = torch.device("cuda", d.local)
+    torch.cuda.set_device(dev)
+    if d.rank == 0:  # one build per node: the other ranks wait, then load it
+        _build.build()
+    d.barrier()
+    r = measure_float(d, dev, args.steps, args.warmup)
+    if d.rank == 0:
+        line = {"metric": METRIC, "value": r["blocks_s"], "unit": "blocks/s", "n_gpus": d.ws, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic N(0,1)",
+                "config": r["config"], "gbs": r["gbs"], "hbm_frac": r["gbs"] / measured_peaks()[0],
+                "roofline": r["roofline"], "gpu_launches": r["gpu_launches"]}
+        print(json.dumps(line), flush=True)
     d.close()
     return 0
 
@@ -779,31 +853,31 @@ def run_float(args):
 SERVING_MAX_RATE = 5000  # the workload's offered rates run from 100 to 5000 req/s
 
 
-def run_serving(args):
+SERVING_SIZES = [(256, 256), (512, 512), (1080, 1920), (2160, 3840), (4096, 4096)]
+
+
+def measure_serving(dev, native_rates, python_rates=(), duration=1.5):
     """Poisson stream of encode/decode requests (50/50) of sizes uniform over
-    {256^2, 512^2, 1080x1920, 2160x3840, 4096^2}, 4 GB device budget; the
-    native scheduler (adct_server_*) and the Python one side by side."""
+    SERVING_SIZES, 4 GB device budget, `duration` seconds per offered rate:
+    the native scheduler (adct_server_*) at native_rates and the Python one
+    at python_rates.  One row per rate: completed req/s, p50/p99 latency,
+    errors, pixel throughput and the client's own submission lateness."""
     import gc
 
     import numpy as np
     import torch
 
-    from paper_1702_00817_gb300 import _build, inputs
+    from paper_1702_00817_gb300 import inputs
     from paper_1702_00817_gb300.serve import NativeServer, Server, poisson_run
-    d = Dist()
-    dev = torch.device("cuda", d.local)
-    torch.cuda.set_device(dev)
-    if d.rank == 0:  # one build per node: the other ranks wait, then load it
-        _build.build()
-    d.barrier()
-    sizes = [(256, 256), (512, 512), (1080, 1920), (2160, 3840), (4096, 4096)]
+    sizes = SERVING_SIZES
     imgs = {hw: [inputs.synth_image_device(hw[0], hw[1], 7000 + 10 * i + k, 1, dev)[0].cpu().pin_memory()
                  for k in range(2)] for i, hw in enumerate(sizes)}
-    duration = 1.5
     results = {}
-    for name, cls, rates, spin in (("native", NativeServer, (100, 500, 1000, 2000, 5000, 10000, 20000), True),
-                                   ("python", Server, (100, 500, 1000, 2000, 5000), False)):
-        srv = cls(d.local, budget_bytes=4 << 30, streams=4)
+    for name, cls, rates, spin in (("native", NativeServer, native_rates, True),
+                                   ("python", Server, python_rates, False)):
+        if not rates:
+            continue
+        srv = cls(dev.index, budget_bytes=4 << 30, streams=4)
         if hasattr(srv, "warm_host_buffers"):
             srv.warm_host_buffers(sizes, count=48)
         else:
@@ -814,24 +888,46 @@ def run_serving(args):
         rows = []
         gc.collect()
         gc.disable()  # a collection pause inside the run would be charged to whichever request it hit
-        for rate in rates:
-            n_req = max(20, int(rate * duration))
-            t0 = time.perf_counter()
-            reqs = poisson_run(srv, rate=float(rate), n_requests=n_req, sizes=sizes, images_by_size=imgs, seed=rate,
-                               spin=spin)
-            wall = max(r.t_done for r in reqs) - t0
-            ok = [r for r in reqs if r.error is None]
-            lat = np.array([r.latency for r in ok]) * 1000.0
-            late = np.array([r.t_sent - r.t_arrival for r in reqs]) * 1000.0  # client lateness, inside the latency
-            px = sum(r.pixels.numel() if r.kind == "encode" else r.out_pixels for r in ok)
-            rows.append({"offered_req_s": rate, "req_s": len(ok) / wall, "p50_ms": float(np.percentile(lat, 50)),
-                         "p99_ms": float(np.percentile(lat, 99)), "errors": len(reqs) - len(ok),
-                         "blocks_s": px / 64 / wall, "client_late_p99_ms": float(np.percentile(late, 99)),
-                         "client_late_max_ms": float(late.max()),
-                         "client_submit_max_ms": float(max(r.t_submitted - r.t_sent for r in reqs) * 1000.0)})
-        gc.enable()
+        try:
+            for rate in rates:
+                n_req = max(20, int(rate * duration))
+                t0 = time.perf_counter()
+                reqs = poisson_run(srv, rate=float(rate), n_requests=n_req, sizes=sizes, images_by_size=imgs,
+                                   seed=rate, spin=spin)
+                wall = max(r.t_done for r in reqs) - t0
+                ok = [r for r in reqs if r.error is None]
+                lat = np.array([r.latency for r in ok]) * 1000.0
+                late = np.array([r.t_sent - r.t_arrival for r in reqs]) * 1000.0  # client lateness, inside the latency
+                px = sum(r.pixels.numel() if r.kind == "encode" else r.out_pixels for r in ok)
+                rows.append({"offered_req_s": rate, "req_s": len(ok) / wall,
+                             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                             "errors": len(reqs) - len(ok), "requests": len(reqs), "blocks_s": px / 64 / wall,
+                             "client_late_p99_ms": float(np.percentile(late, 99)),
+                             "client_late_max_ms": float(late.max()),
+                             "client_submit_max_ms": float(max(r.t_submitted - r.t_sent for r in reqs) * 1000.0)})
+        finally:
+            gc.enable()
         results[name] = {"rows": rows, "stats": dict(srv.stats)}
         srv.close()
+    del imgs
+    torch.cuda.empty_cache()
+    return results
+
+
+def run_serving(args):
+    """Serving at offered rates 100..5000 req/s (the workload) plus two overload rates."""
+    import torch
+
+    from paper_1702_00817_gb300 import _build
+    d = Dist()
+    dev = torch.device("cuda", d.local)
+    torch.cuda.set_device(dev)
+    if d.rank == 0:  # one build per node: the other ranks wait, then load it
+        _build.build()
+    d.barrier()
+    duration = 1.5
+    results = measure_serving(dev, (100, 500, 1000, 2000, 5000, 10000, 20000), (100, 500, 1000, 2000, 5000),
+                              duration)
     if d.rank == 0:
         # headline: the highest offered rate of the workload (100-5000 req/s); the
         # rates above it are reported as overload rows
@@ -841,9 +937,7 @@ def run_serving(args):
         line = {"metric": METRIC, "value": top["req_s"], "unit": "req/s", "n_gpus": d.ws,
                 "steps": len(inside), "warmup": 1, "ms_per_step": None, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-                "config": {"workload": "serving: Poisson encode/decode 50/50, sizes {256^2,512^2,1080x1920,"
-                                       "2160x3840,4096^2}, 4 GB budget, on-device coefficient store; native "
-                                       "scheduler (adct_server_*), Python scheduler for comparison",
+                "config": {"workload": SERVING_WORKLOAD + "; Python scheduler for comparison",
                            "seconds_per_rate": duration, "headline_offered_req_s": top["offered_req_s"]},
                 "serving": inside, "p50_ms": top["p50_ms"], "p99_ms": top["p99_ms"], "errors": top["errors"],
                 "overload": [r for r in rows_n if r["offered_req_s"] > SERVING_MAX_RATE],
@@ -851,6 +945,10 @@ def run_serving(args):
         print(json.dumps(line), flush=True)
     d.close()
     return 0
+
+
+SERVING_WORKLOAD = ("serving: Poisson encode/decode 50/50, sizes {256^2,512^2,1080x1920,2160x3840,4096^2} u8, "
+                    "4 GB budget, on-device coefficient store, native scheduler (adct_server_*)")
 
 
 def run_quality(args):

@@ -240,10 +240,14 @@ adct_status adct_get_launch(adct_context* ctx, adct_launch* launch);
 /*
  * Round trip through a CUDA graph cached in ctx per batch signature (image
  * count, sizes, channel counts, quantiser mode, launch shape and which of
- * coef/dst are used).  The first call with a signature captures
- * {descriptor upload; kernel}; later calls rewrite the pinned descriptor
- * staging buffer and replay.  Results are identical to adct_roundtrip.
- * *replayed (nullable) is set to 1 when a cached graph was replayed.
+ * coef/dst are used).  The first call with a signature captures the kernel
+ * launches (one per pixel layout class) reading a descriptor table owned by
+ * the graph; each call uploads that table on `stream` only when it differs
+ * from the one already on the device (other buffers of the same shapes),
+ * after waiting on the host for the graph's previous replay, and then
+ * replays.  A batch replayed on the same buffers uploads nothing and does not
+ * wait.  Results are identical to adct_roundtrip.  *replayed (nullable) is
+ * set to 1 when a cached graph was replayed.
  */
 adct_status adct_roundtrip_graph(adct_context* ctx, const adct_image* imgs, int32_t n, const adct_quant* quant,
                                  adct_stream_t stream, int32_t* replayed);
