@@ -525,7 +525,9 @@ adct_status float_params(adct_context* ctx, const float* Qsoft, FloatParams& fp)
     const float Q = Qsoft[k];
     if (!(Q > 0.0f) || !std::isfinite(Q)) return fail(ctx, ADCT_ERR_INVALID_ARG, "Qsoft entries must be positive");
     fp.c2pi[k] = (float)((double)Q / (2.0 * M_PI));
-    fp.r2[k] = (float)(2.0 / (double)Q);
+    fp.rq[k] = (float)(1.0 / (double)Q);
+    // d_i d_j = 2^-((a_i + a_j) / 2), Sec. 2 matrix D
+    fp.g[k] = (float)(std::pow(2.0, -0.5 * (scale_exp(k / 8) + scale_exp(k % 8))) / (double)Q);
   }
   return ADCT_OK;
 }

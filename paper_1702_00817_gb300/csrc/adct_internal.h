@@ -82,9 +82,13 @@ cudaError_t launch_dct_quality(const PlaneDesc* planes, const int64_t* starts, i
                                cudaStream_t stream);
 
 // Float variant (Sec. 2 C^ = D T): forward (optionally soft-quantised) and adjoint.
+// Per position k = 8 i + j with soft step Q_k: the soft quantiser's phase is
+// 2 pi h with h = y / Q_k = v d_i d_j / Q_k (v the unscaled coefficient
+// T x T^T): the forward forms it as y rq, the adjoint as v g.
 struct FloatParams {
   float c2pi[64];  // Q / (2 pi)
-  float r2[64];    // 2 / Q  (sin(2 pi y / Q) = sinpi(y * 2 / Q))
+  float rq[64];    // 1 / Q
+  float g[64];     // d_i d_j / Q
 };
 cudaError_t launch_float_forward(const float* x, float* y, int64_t planes, int32_t H, int32_t W,
                                  const FloatParams* fp, int sm_count, cudaStream_t stream);
