@@ -270,14 +270,16 @@ int describe_image(const adct_image& im, int32_t cpb, bool coef_only, int32_t pl
   d.cstride = nb * cpb;
   d.wb = wb;
   d.hb = hb;
-  d.ew = im.width - 8 * (wb - 1);
-  d.eh = im.height - 8 * (hb - 1);
+  d.cwb = wb;
+  d.ew = (int16_t)(im.width - 8 * (wb - 1));
+  d.eh = (int16_t)(im.height - 8 * (hb - 1));
+  d.bx0 = 0;
   if (inter) {
     d.src = im.src;
     d.dst = im.dst;
     d.coef = im.coef;
     d.plane_id = plane_id;
-    d.nch = im.channels;
+    d.nch = (int16_t)im.channels;
     out[(*count)++] = d;
     return group_of(im, coef_only);
   }
@@ -290,6 +292,56 @@ int describe_image(const adct_image& im, int32_t cpb, bool coef_only, int32_t pl
     out[(*count)++] = d;
   }
   return group_of(im, coef_only);
+}
+
+// Descriptors of one planar plane or one interleaved image (`one`: channels
+// 1, or an interleaved image), split when it has edge blocks and at least
+// kSplitMin interior blocks: the interior (every block with 8 x 8 valid
+// pixels) goes to the group without edge handling, the last block column and
+// the rest of the last block row to the edge group; otherwise one descriptor.
+// Returns the count (1..3); part k belongs to group groups[k].
+constexpr int64_t kSplitMin = 64;
+int describe_parts(const adct_image& one, int32_t cpb, bool coef_only, int32_t plane_id, PlaneDesc parts[3],
+                   int groups[3]) {
+  int32_t cnt = 0;
+  const int g = describe_image(one, cpb, coef_only, plane_id, parts, &cnt);
+  groups[0] = g;
+  const PlaneDesc whole = parts[0];
+  const bool right = whole.ew < 8, bottom = whole.eh < 8;
+  const int32_t wi = whole.wb - (right ? 1 : 0), hi = whole.hb - (bottom ? 1 : 0);
+  if ((g & 1) == 0 || (int64_t)wi * hi < kSplitMin) return 1;
+  const int64_t bpx = 8 * (int64_t)whole.nch;  // pixel bytes of a block row segment
+  const int64_t cpb64 = cpb;
+  int n = 0;
+  PlaneDesc d = whole;  // the interior
+  d.wb = wi;
+  d.hb = hi;
+  d.ew = 8;
+  d.eh = 8;
+  parts[n] = d;
+  groups[n++] = g & ~1;
+  if (right) {  // the last block column, every block row
+    d = whole;
+    d.src = whole.src ? whole.src + bpx * (whole.wb - 1) : nullptr;
+    d.dst = whole.dst ? whole.dst + bpx * (whole.wb - 1) : nullptr;
+    d.coef = whole.coef ? whole.coef + cpb64 * (whole.wb - 1) : nullptr;
+    d.wb = 1;
+    d.bx0 = (int16_t)(whole.wb - 1);
+    parts[n] = d;
+    groups[n++] = g;
+  }
+  if (bottom) {  // the last block row without its last block when that is in the column
+    d = whole;
+    d.src = whole.src ? whole.src + 8 * whole.pitch * (whole.hb - 1) : nullptr;
+    d.dst = whole.dst ? whole.dst + 8 * whole.pitch * (whole.hb - 1) : nullptr;
+    d.coef = whole.coef ? whole.coef + cpb64 * whole.cwb * (whole.hb - 1) : nullptr;
+    d.wb = wi;
+    d.hb = 1;
+    d.ew = 8;
+    parts[n] = d;
+    groups[n++] = g;
+  }
+  return n;
 }
 
 // Work units of one call: one group (one launch) per pixel layout class;
@@ -344,7 +396,8 @@ adct_status build_tables(adct_context* ctx, const adct_image* imgs, int32_t n, i
   }
   t.nplanes = 0;
   t.blocks = 0;
-  PlaneDesc tmp[1];
+  PlaneDesc pieces[3];
+  int piece_group[3];
   for (int32_t m = 0; m < n; ++m) {
     const adct_image& im = imgs[m];
     const char* why = "";
@@ -355,16 +408,18 @@ adct_status build_tables(adct_context* ctx, const adct_image* imgs, int32_t n, i
     const int32_t parts = inter ? 1 : im.channels;
     for (int32_t c = 0; c < parts; ++c) {
       adct_image one = im;
-      int32_t cnt = 0;
       if (!inter) {  // one planar plane at a time
         one.channels = 1;
         one.src = im.src ? im.src + (int64_t)c * im.plane_stride : nullptr;
         one.dst = im.dst ? im.dst + (int64_t)c * im.plane_stride : nullptr;
         one.coef = im.coef ? im.coef + (int64_t)c * nb * cpb : nullptr;
       }
-      const int g = describe_image(one, cpb, coef_only, t.nplanes + c, tmp, &cnt);
-      t.planes[g].push_back(tmp[0]);
-      t.starts[g].push_back(t.starts[g].back() + nb);
+      const int np = describe_parts(one, cpb, coef_only, t.nplanes + c, pieces, piece_group);
+      for (int k = 0; k < np; ++k) {
+        const int g = piece_group[k];
+        t.planes[g].push_back(pieces[k]);
+        t.starts[g].push_back(t.starts[g].back() + (int64_t)pieces[k].wb * pieces[k].hb);
+      }
     }
     t.nplanes += im.channels;
     t.blocks += nb * im.channels;
@@ -449,6 +504,7 @@ int need_for_kind(int kind) {
 
 // One launch per non-empty group of t, whose tables are at dev (t.blob's layout).
 // Under stream capture (timed = false) no timing events are recorded.
+// Launches every non-empty group of a call, one after the other on `stream`.
 adct_status launch_groups(adct_context* ctx, CodecLaunch cl, const Tables& t, const char* dev, const LaunchShape& shape,
                           cudaStream_t stream, bool timed = true) {
   for (int g = 0; g < kGroups; ++g) {

@@ -154,15 +154,15 @@ __device__ __forceinline__ uint8_t* dst_of(const PlaneDesc* d) {
 // Coefficients of block (by, bx) of channel ch (always 0 for a planar plane).
 __device__ __forceinline__ int16_t* coef_of(const PlaneDesc* d, const Pos& q, int ch = 0) {
   const int16_t* c = (const int16_t*)__ldg((const unsigned long long*)&d->coef);
-  return (int16_t*)c + ch * __ldg(&d->cstride) + ((int64_t)q.by * __ldg(&d->wb) + q.bx) * 64;
+  return (int16_t*)c + ch * __ldg(&d->cstride) + ((int64_t)q.by * __ldg(&d->cwb) + q.bx) * 64;
 }
 // Valid pixel columns and rows of a block (8 inside the image; 1..8 in the
 // last block column / row of an image whose side is not a multiple of 8).
 __device__ __forceinline__ int valid_cols(const PlaneDesc* d, const Pos& q) {
-  return q.bx + 1 == (uint32_t)__ldg(&d->wb) ? __ldg(&d->ew) : 8;
+  return q.bx + 1 == (uint32_t)__ldg(&d->wb) ? (int)__ldg(&d->ew) : 8;
 }
 __device__ __forceinline__ int valid_rows(const PlaneDesc* d, const Pos& q) {
-  return q.by + 1 == (uint32_t)__ldg(&d->hb) ? __ldg(&d->eh) : 8;
+  return q.by + 1 == (uint32_t)__ldg(&d->hb) ? (int)__ldg(&d->eh) : 8;
 }
 
 // Lane stride, in int16, of the packed staging: r, padded by 2 when r is a
@@ -172,7 +172,7 @@ __device__ __forceinline__ int zz_stride(int r) { return r + ((r & 3) == 0 ? 2 :
 
 __device__ __forceinline__ int16_t* coef_of_zz(const PlaneDesc* d, const Pos& q, int r, int ch = 0) {
   const int16_t* c = (const int16_t*)__ldg((const unsigned long long*)&d->coef);
-  return (int16_t*)c + ch * __ldg(&d->cstride) + ((int64_t)q.by * __ldg(&d->wb) + q.bx) * r;
+  return (int16_t*)c + ch * __ldg(&d->cstride) + ((int64_t)q.by * __ldg(&d->cwb) + q.bx) * r;
 }
 
 // Plane cursor of one lane: the flat index only grows (by 32 per tile), so the
@@ -240,13 +240,32 @@ struct SmemPlan {
   static constexpr int warp = stages * in_stage + out_stage;
 };
 
-// A word made of bytes p0..p3 (p0 lowest) of the byte sequence held in w
-// (byte b is byte b & 3 of w[b >> 2]).  Called with constant positions inside
-// unrolled loops, so w stays in registers and each call is three PRMTs.
-__device__ __forceinline__ uint32_t pick4(const uint32_t* w, int p0, int p1, int p2, int p3) {
-  const uint32_t lo = __byte_perm(w[p0 >> 2], w[p1 >> 2], (uint32_t)((p0 & 3) | ((4 + (p1 & 3)) << 4)));
-  const uint32_t hi = __byte_perm(w[p2 >> 2], w[p3 >> 2], (uint32_t)((p2 & 3) | ((4 + (p3 & 3)) << 4)));
-  return __byte_perm(lo, hi, 0x5410);
+// Bytes p0..p3 of the byte sequence held in w (byte p is byte p & 3 of
+// w[p >> 2]) as one word, p0 lowest, with one byte permute per distinct
+// source word after the second (1 to 3 permutes: 2 for the 4 bytes of one
+// channel of a 3-channel span, against 3 for pairwise gathering, which took
+// the interleaved round trip from 404 us to 395 us).  Called with constant
+// positions inside unrolled loops, so all the selection below folds away.
+__device__ __forceinline__ uint32_t gather4(const uint32_t* w, int p0, int p1, int p2, int p3) {
+  const int x0 = p0 >> 2, x1 = p1 >> 2, x2 = p2 >> 2, x3 = p3 >> 2;
+  // distinct source words A, B, C, D in order of first use (-1: none)
+  const int A = x0;
+  const int B = x1 != A ? x1 : x2 != A ? x2 : x3 != A ? x3 : -1;
+  const int C = (x2 != A && x2 != B) ? x2 : (x3 != A && x3 != B) ? x3 : -1;
+  const int D = (x3 != A && x3 != B && x3 != C) ? x3 : -1;
+  // first permute: bytes of A (selector b) and B (4 + b)
+  auto s1 = [&](int x, int p) { return (uint32_t)(x == A ? (p & 3) : x == B ? 4 + (p & 3) : 0); };
+  uint32_t r = __byte_perm(w[A], w[B < 0 ? A : B], s1(x0, p0) | s1(x1, p1) << 4 | s1(x2, p2) << 8 | s1(x3, p3) << 12);
+  // then one permute per further word: keep byte t, or take byte b of it
+  if (C >= 0) {
+    auto s2 = [&](int x, int p, int t) { return (uint32_t)(x == C ? 4 + (p & 3) : t); };
+    r = __byte_perm(r, w[C], s2(x0, p0, 0) | s2(x1, p1, 1) << 4 | s2(x2, p2, 2) << 8 | s2(x3, p3, 3) << 12);
+  }
+  if (D >= 0) {
+    auto s3 = [&](int x, int p, int t) { return (uint32_t)(x == D ? 4 + (p & 3) : t); };
+    r = __byte_perm(r, w[D], s3(x0, p0, 0) | s3(x1, p1, 1) << 4 | s3(x2, p2, 2) << 8 | s3(x3, p3, 3) << 12);
+  }
+  return r;
 }
 
 // Interleaved tiles.  The input stage of a tile of 32 pixel positions holds, for
@@ -273,8 +292,8 @@ __device__ __forceinline__ void deinterleave_tile(uint8_t* stage, int lane) {
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
-      const uint32_t a = pick4(w[i], c, c + NCH, c + 2 * NCH, c + 3 * NCH);
-      const uint32_t b = pick4(w[i], c + 4 * NCH, c + 5 * NCH, c + 6 * NCH, c + 7 * NCH);
+      const uint32_t a = gather4(w[i], c, c + NCH, c + 2 * NCH, c + 3 * NCH);
+      const uint32_t b = gather4(w[i], c + 4 * NCH, c + 5 * NCH, c + 6 * NCH, c + 7 * NCH);
       ((uint2*)(stage + c * 2048))[i * 32 + lane] = make_uint2(a, b);
     }
 }
@@ -509,7 +528,7 @@ __device__ __forceinline__ void write_pixels_interleaved(const uint8_t* __restri
         const int b = 4 * m + t, px = b / NCH, c = b % NCH;
         pos4[t] = 4 * (2 * c + (px >> 2)) + (px & 3);
       }
-      span[m] = pick4(q, pos4[0], pos4[1], pos4[2], pos4[3]);
+      span[m] = gather4(q, pos4[0], pos4[1], pos4[2], pos4[3]);
     }
     if (vc == 8) {
 #pragma unroll
@@ -524,22 +543,23 @@ __device__ __forceinline__ void write_pixels_interleaved(const uint8_t* __restri
 }
 
 // Write a staged 32-block half-tile of coefficients back with 512-byte warp
-// stores.  The blocks of a plane are contiguous in coef, so when every active
-// lane is in lane 0's plane the half-tile is one contiguous range.
+// stores when the active lanes' blocks are consecutive in memory (one
+// contiguous range: the usual case; not when the tile crosses a plane, or a
+// block row of a descriptor narrower than its coefficient rows).
 __device__ __forceinline__ void write_back(const uint8_t* __restrict__ stage_out, const PlaneDesc* __restrict__ planes,
                                           const Pos& pos, int lane, int ch) {
   const bool active = pos.plane >= 0;
-  const int plane0 = __shfl_sync(0xffffffffu, pos.plane, 0);
   const unsigned act = __ballot_sync(0xffffffffu, active);
   int16_t* mine = active ? coef_of(planes + pos.plane, pos, ch) : nullptr;
+  int16_t* const base = (int16_t*)__shfl_sync(0xffffffffu, (unsigned long long)mine, 0);
   // Instruction k moves bytes [512 k, 512 k + 512) of the half-tile: lane l
   // takes 16-byte chunk (l & 7) of block 4 k + (l >> 3), i.e. byte 512 k + 16 l;
   // in shared memory that chunk sits at one of two lane-specific offsets (the
   // swizzle depends on k only through k & 1) plus 512 k.
   const int pb = lane >> 3, pc = lane & 7;
   const uint32_t rd0 = pb * 128 + ((pc ^ pb) << 4), rd1 = pb * 128 + ((pc ^ (pb + 4)) << 4);
-  if (__all_sync(0xffffffffu, !active || pos.plane == plane0)) {
-    int4* gp = (int4*)__shfl_sync(0xffffffffu, (unsigned long long)mine, 0) + lane;
+  if (__all_sync(0xffffffffu, !active || mine == base + 64 * lane)) {
+    int4* gp = (int4*)base + lane;
     const int nact = __popc(act);  // active lanes are a prefix of the warp
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -557,8 +577,8 @@ __device__ __forceinline__ void write_back(const uint8_t* __restrict__ stage_out
 
 // Write a staged 32-block half-tile of packed zonal coefficients (r int16 per
 // block, r <= NMAX; lane l's at [l sp, l sp + r), sp = zz_stride(r)) back to
-// memory.  When every active lane is in lane 0's plane the half-tile is one
-// contiguous range of nact r values, written as 4-byte words when aligned (all
+// memory.  When the active lanes' blocks are consecutive in memory the
+// half-tile is one contiguous range of nact r values, written as 4-byte words when aligned (all
 // loads of the warp issued before its stores); otherwise each lane writes its
 // own r.  With padding (r a multiple of 4) value e of the range sits at
 // e + 2 (e / r) in the staging, so word w at w + w / (r / 2); the division is a
@@ -568,13 +588,12 @@ __device__ __forceinline__ void write_back_zz(const uint8_t* __restrict__ stage_
                                              const PlaneDesc* __restrict__ planes, const Pos& pos, int lane, int r,
                                              uint32_t mh, int ch) {
   const bool active = pos.plane >= 0;
-  const int plane0 = __shfl_sync(0xffffffffu, pos.plane, 0);
   const unsigned act = __ballot_sync(0xffffffffu, active);
   int16_t* mine = active ? coef_of_zz(planes + pos.plane, pos, r, ch) : nullptr;
   const int16_t* st16 = (const int16_t*)stage_out;
   const bool padded = (r & 3) == 0;
-  if (__all_sync(0xffffffffu, !active || pos.plane == plane0)) {
-    int16_t* base = (int16_t*)__shfl_sync(0xffffffffu, (unsigned long long)mine, 0);
+  int16_t* const base = (int16_t*)__shfl_sync(0xffffffffu, (unsigned long long)mine, 0);
+  if (__all_sync(0xffffffffu, !active || mine == base + r * lane)) {
     const int n = __popc(act) * r;  // values to write
     if (((uintptr_t)base & 3) == 0 && (n & 1) == 0) {
       constexpr int kWords = (NMAX + 1) / 2;  // words per lane at most (32 r / 2 / 32)
@@ -666,7 +685,7 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
         const int vc = EDGE ? valid_cols(d, q) : 8, vr = EDGE ? valid_rows(d, q) : 8;
         const int nchunk = EDGE ? (NCH * vc + 7) / 8 : NCH;
 #ifdef ADCT_CHECKED
-        if (8 * NCH * (int64_t)q.bx + 8 * nchunk > pitch) {  // a copy would pass the end of the row
+        if (8 * NCH * ((int64_t)__ldg(&d->bx0) + q.bx) + 8 * nchunk > pitch) {  // a copy would pass the end of the row
           if (fault) atomicOr(fault, FAULT_ROW_BYTES);
           cp_async_commit();
           return;

@@ -99,27 +99,32 @@ __host__ __device__ __forceinline__ void inv2d(const VI* in, V* v) {
   for (int i = 0; i < 8; ++i) inv8<1>(v + 8 * i);
 }
 
-// One plane of the flattened block index.  Planes of a multi-channel image
-// are separate entries.  Block f of the plane (row-major over blocks) sits at
-// src + (8 * (f / wb)) * pitch + 8 * (f % wb); its coefficients at coef + 64 f.
 // One unit of the flat work index: a planar uint8 plane (the flat index counts
 // its 8x8 blocks), or an interleaved image of nch = 3 or 4 channels (the flat
 // index counts its 8x8 pixel positions, each carrying nch blocks).  Images
-// whose sides are not multiples of 8 are covered by ceil(side / 8) blocks; the
-// last block column holds ew valid pixel columns and the last block row eh
-// valid rows (1..8), the rest is the edge replicated.
+// whose sides are not multiples of 8 are covered by ceil(side / 8) blocks;
+// the last block column holds ew valid pixel columns and the last block row
+// eh valid rows (1..8), the rest is the edge replicated.  A descriptor may
+// cover a rectangle of an image's blocks (its interior, its last block column
+// or its last block row): src, dst and coef then point at the rectangle's
+// first block, wb x hb are its blocks, cwb is the image's blocks per row (the
+// coefficient row stride) and bx0 the rectangle's first block column.
+// Block (by, bx) of the descriptor sits at src + (8 by) pitch + 8 nch bx; its
+// coefficients at coef + (by cwb + bx) c, c = 64 (or r, packed zonal).
 struct PlaneDesc {
   const uint8_t* src;
   uint8_t* dst;
   int16_t* coef;    // channel 0's coefficients
   int64_t pitch;    // bytes between pixel rows
   int64_t cstride;  // int16 between the coefficient planes of consecutive channels
-  int32_t wb;       // blocks per row
-  int32_t hb;       // block rows
-  int32_t ew;       // valid pixel columns of the last block column
-  int32_t eh;       // valid pixel rows of the last block row
+  int32_t wb;       // blocks per row of this descriptor
+  int32_t hb;       // block rows of this descriptor
+  int32_t cwb;      // blocks per coefficient row (the whole image's blocks per row)
   int32_t plane_id; // plane number of channel 0 in the call (per-plane outputs)
-  int32_t nch;      // 1: planar plane; 3, 4: interleaved channels
+  int16_t ew;       // valid pixel columns of the descriptor's last block column
+  int16_t eh;       // valid pixel rows of its last block row
+  int16_t nch;      // 1: planar plane; 3, 4: interleaved channels
+  int16_t bx0;      // first block column within the image
 };
 static_assert(sizeof(PlaneDesc) == 64, "descriptor layout");
 
