@@ -137,7 +137,10 @@ typedef struct {
  *                     coefficient output; adct_get_launch then reports 0
  *   stage_coef        0: each thread stores its 128 coefficient bytes directly;
  *                     1: coefficients are staged through shared memory and
- *                        written by the warp as contiguous 512-byte stores
+ *                        written by the warp as contiguous 512-byte stores;
+ *                    -1 (a new context): the library's choice per call, 1
+ *                        except for the packed zonal round trip with r <= 8,
+ *                        whose few coefficients per block go out directly
  *   reserved          must be 0
  */
 typedef struct {

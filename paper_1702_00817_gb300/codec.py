@@ -216,7 +216,7 @@ class Codec:
         N.check(st, self.ctx, "adct_roundtrip_graph", lib=self.lib)
         return bool(rep.value)
 
-    def set_launch(self, threads_per_cta=0, ctas_per_sm=0, stage_coef=1):
+    def set_launch(self, threads_per_cta=0, ctas_per_sm=0, stage_coef=-1):
         l = N.adct_launch(threads_per_cta, ctas_per_sm, stage_coef, 0)
         N.check(self.lib.adct_set_launch(self.ctx, ctypes.byref(l)), self.ctx, "adct_set_launch", lib=self.lib)
 

@@ -62,7 +62,7 @@ struct PipeSlot {
 struct adct_context {
   int device = 0;
   int sm_count = 0;
-  LaunchShape shape{128, 0, 1};  // ctas_per_sm 0: chosen per kernel kind
+  LaunchShape shape{128, 0, -1};  // ctas_per_sm 0, stage_coef -1: chosen per kernel kind
   std::string last_error;
   Slot slots[kSlots];
   int next_slot = 0;
@@ -475,7 +475,7 @@ adct_status acquire_slot(adct_context* ctx, size_t bytes, Slot** out) {
 
 adct_status check_shape(adct_context* ctx, const LaunchShape& sh) {
   if (sh.threads < 32 || sh.threads > 128 || sh.threads % 32 || sh.ctas_per_sm < 0 || sh.ctas_per_sm > 32 ||
-      (sh.stage_coef != 0 && sh.stage_coef != 1))
+      sh.stage_coef < -1 || sh.stage_coef > 1)
     return fail(ctx, ADCT_ERR_INVALID_ARG, "launch shape out of range");
   return ADCT_OK;
 }

@@ -46,23 +46,44 @@ KernelFn pick_kernel(int kind, int qmode, bool evenq) {
   return evenq ? pick_kernel_q<true>(kind, qmode) : pick_kernel_q<false>(kind, qmode);
 }
 
+// Packed zonal layout with r = 64 (the dense layout in zig-zag order).
+KernelFn pick_zz64(int kind) {
+  switch (kind) {
+    case K_RT_FULL: return k_codec<K_RT_FULL, QM_ZONAL_ZZ, false, kZoneZZ64>;
+    case K_RT_COEF: return k_codec<K_RT_COEF, QM_ZONAL_ZZ, false, kZoneZZ64>;
+    case K_INVERSE: return k_codec<K_INVERSE, QM_ZONAL_ZZ, false, kZoneZZ64>;
+    default: return nullptr;
+  }
+}
+
 }  // namespace
 
 namespace {
-template <int NCH>
-int warp_smem_n(int kind) {
+template <int NCH, int ZS>
+int warp_smem_z(int kind) {
   switch (kind) {
-    case K_FORWARD: return SmemPlan<K_FORWARD, NCH>::warp;
-    case K_QUANTISE: return SmemPlan<K_QUANTISE, NCH>::warp;
-    case K_INVERSE: return SmemPlan<K_INVERSE, NCH>::warp;
-    case K_RT_FULL: return SmemPlan<K_RT_FULL, NCH>::warp;
-    case K_RT_PIX: return SmemPlan<K_RT_PIX, NCH>::warp;
-    case K_RT_SSE: return SmemPlan<K_RT_SSE, NCH>::warp;
-    default: return SmemPlan<K_RT_COEF, NCH>::warp;
+    case K_FORWARD: return SmemPlan<K_FORWARD, NCH, ZS>::warp;
+    case K_QUANTISE: return SmemPlan<K_QUANTISE, NCH, ZS>::warp;
+    case K_INVERSE: return SmemPlan<K_INVERSE, NCH, ZS>::warp;
+    case K_RT_FULL: return SmemPlan<K_RT_FULL, NCH, ZS>::warp;
+    case K_RT_PIX: return SmemPlan<K_RT_PIX, NCH, ZS>::warp;
+    case K_RT_SSE: return SmemPlan<K_RT_SSE, NCH, ZS>::warp;
+    default: return SmemPlan<K_RT_COEF, NCH, ZS>::warp;
   }
 }
-int warp_smem(int kind, int nch) {
-  return nch == 3 ? warp_smem_n<3>(kind) : nch == 4 ? warp_smem_n<4>(kind) : warp_smem_n<1>(kind);
+static_assert(ADCT_DEEP_ZONE <= 4, "warp_smem tells zones 0..4 apart only");
+// Shared memory per warp of the kernel for this kind, channel count and zone.
+int warp_smem(int kind, int nch, int zs) {
+  if (nch == 3) return warp_smem_z<3, 14>(kind);
+  if (nch == 4) return warp_smem_z<4, 14>(kind);
+  switch (zs) {
+    case 0: return warp_smem_z<1, 0>(kind);
+    case 1: return warp_smem_z<1, 1>(kind);
+    case 2: return warp_smem_z<1, 2>(kind);
+    case 3: return warp_smem_z<1, 3>(kind);
+    case 4: return warp_smem_z<1, 4>(kind);
+    default: return warp_smem_z<1, 14>(kind);
+  }
 }
 }  // namespace
 
@@ -73,8 +94,8 @@ int warp_smem(int kind, int nch) {
 // the kernels that use more than 128 registers.
 int default_ctas_per_sm(int kind, int qmode) { return (kind == K_RT_COEF && qmode != QM_ZONAL_ZZ) ? 3 : 4; }
 
-size_t codec_smem_bytes(const LaunchShape& shape, int kind, int nch) {
-  return (size_t)(shape.threads / 32) * warp_smem(kind, nch);
+size_t codec_smem_bytes(const LaunchShape& shape, int kind, int nch, int zs) {
+  return (size_t)(shape.threads / 32) * warp_smem(kind, nch, zs);
 }
 
 int codec_grid(const LaunchShape& shape, int sm_count, int64_t total) {
@@ -87,6 +108,7 @@ int codec_grid(const LaunchShape& shape, int sm_count, int64_t total) {
 cudaError_t launch_codec(const CodecLaunch& c, const LaunchShape& shape, int sm_count, cudaStream_t stream) {
   if (c.total <= 0) return cudaSuccess;
   KernelFn fn = nullptr;
+  int zs = 14;  // zone of the kernel picked (its shared-memory plan)
   if (c.nch == 3 || c.nch == 4) {
     fn = c.edge ? pick_interleaved_edge_kernel(c.kind, c.qmode, c.evenq, c.nch)
                 : pick_interleaved_kernel(c.kind, c.qmode, c.evenq, c.nch);
@@ -94,15 +116,23 @@ cudaError_t launch_codec(const CodecLaunch& c, const LaunchShape& shape, int sm_
   } else if (c.edge) {
     fn = pick_edge_kernel(c.kind, c.qmode, c.evenq);
     if (!fn) return cudaErrorInvalidValue;
+  } else if (c.qmode == QM_ZONAL_ZZ && c.qp.r == 64) {
+    fn = pick_zz64(c.kind);
   } else if (c.qmode == QM_ZONAL || c.qmode == QM_ZONAL_ZZ) {
-    const int zs = zone_for(c.qp.r);
-    if (zs <= kZoneLoMax) fn = pick_zonal_kernel_lo(c.kind, c.qmode, zs);
-    else if (zs <= kZoneHiMax) fn = pick_zonal_kernel_hi(c.kind, c.qmode, zs);
+    // The packed round trip takes at least the zone-3 kernel: the lighter
+    // zone 0-2 kernels ran slower on full-size batches although they execute
+    // fewer instructions (r = 1: 231 us against 196 us with the zone-3 kernel,
+    // 256 x 1080x1920), their warps waiting on memory twice as often per issue.
+    int z = zone_for(c.qp.r);
+    if (c.qmode == QM_ZONAL_ZZ && c.kind == K_RT_FULL && z < 3) z = 3;
+    if (z <= kZoneLoMax) fn = pick_zonal_kernel_lo(c.kind, c.qmode, z);
+    else if (z <= kZoneHiMax) fn = pick_zonal_kernel_hi(c.kind, c.qmode, z);
+    if (fn) zs = z;  // a kernel specialised on zone z
   }
   if (!fn) fn = pick_kernel(c.kind, c.qmode, c.evenq);
   if (!fn) return cudaErrorInvalidValue;
   if (shape.threads < 32 || shape.threads > kMaxThreads || shape.threads % 32) return cudaErrorInvalidValue;
-  const size_t smem = codec_smem_bytes(shape, c.kind, c.nch);
+  const size_t smem = codec_smem_bytes(shape, c.kind, c.nch, zs);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -118,8 +148,13 @@ cudaError_t launch_codec(const CodecLaunch& c, const LaunchShape& shape, int sm_
   const int64_t warps = (int64_t)grid * (shape.threads / 32);
   int64_t chunk = (c.total + warps - 1) / warps;
   chunk = (chunk + kTile - 1) / kTile * kTile;
-  fn<<<grid, shape.threads, smem, stream>>>(c.planes, c.starts, c.nplanes, c.total, chunk, shape.stage_coef, c.sse,
-                                            c.fault, c.qp);
+  // staging of the coefficients: the caller's choice, else staged except for
+  // the packed round trip with r <= 8, whose direct stores measured faster
+  // (r = 1: 185 us against 196 us staged; r = 10: 225 us against 211 us)
+  const int stage = shape.stage_coef >= 0 ? shape.stage_coef
+                                          : (c.qmode == QM_ZONAL_ZZ && c.kind == K_RT_FULL && c.qp.r <= 8) ? 0 : 1;
+  fn<<<grid, shape.threads, smem, stream>>>(c.planes, c.starts, c.nplanes, c.total, chunk, stage, c.sse, c.fault,
+                                            c.qp);
   return cudaGetLastError();
 }
 

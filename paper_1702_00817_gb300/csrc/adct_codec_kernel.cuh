@@ -221,6 +221,13 @@ struct Cursor {
 // same and the shared memory per CTA doubles.)
 constexpr int kTile = 32;
 
+// Marker zone of the packed zonal layout with r = 64: every coefficient is
+// kept and stored in zig-zag order, 128 bytes per block like the dense
+// layout, so these kernels stage and read coefficients as the dense ones do
+// (16-byte chunks, 512-byte warp copies), with the zig-zag order a renaming
+// of registers.
+constexpr int kZoneZZ64 = 15;
+
 // Input stages per warp: while tile i is computed the copies of tiles
 // i + 1 .. i + stages - 1 are in flight.  Two stages measured best: a third
 // stage for pixel input (4 KB in flight per warp) made the kernels with the
@@ -231,9 +238,15 @@ constexpr int kTile = 32;
 // in place as NCH planar tiles of 2 KB; each channel's reconstruction goes back
 // into its planar tile before the rows are re-interleaved and stored.  The
 // inverse from coefficients uses the stage only for the reconstruction.
-template <int KIND, int NCH = 1>
+#ifndef ADCT_DEEP_ZONE
+#define ADCT_DEEP_ZONE -1  // zonal kernels of zones up to this one get ADCT_DEEP_STAGES input stages
+#endif
+#ifndef ADCT_DEEP_STAGES
+#define ADCT_DEEP_STAGES 2
+#endif
+template <int KIND, int NCH = 1, int ZS = 14>
 struct SmemPlan {
-  static constexpr int stages = 2;
+  static constexpr int stages = (KindTraits<KIND>::in_pix && NCH == 1 && ZS <= ADCT_DEEP_ZONE) ? ADCT_DEEP_STAGES : 2;
   static constexpr int in_stage =
       (KindTraits<KIND>::in_pix || NCH > 1) ? 2048 * NCH : 4096;  // one 32-block (or 32-position) tile of input
   static constexpr int out_stage = KindTraits<KIND>::write_coef ? kTileBytesOut : 0;
@@ -350,7 +363,7 @@ __device__ __forceinline__ uint32_t block_step(uint8_t* __restrict__ in, uint8_t
       }
     }
     fwd2d(v);  // Z + 8192 e0 e0^T (raw pixels; the level shift lives in the constants)
-  } else if (QMODE == QM_ZONAL_ZZ) {
+  } else if (QMODE == QM_ZONAL_ZZ && ZS != kZoneZZ64) {
     // packed input: the first r zig-zag coefficients of this block
     constexpr ZigZag zz = make_zigzag();
     const int16_t* c = coef_of_zz(d, pos, qp.r, ch);
@@ -370,18 +383,37 @@ __device__ __forceinline__ uint32_t block_step(uint8_t* __restrict__ in, uint8_t
       v[8 * t + 6] = sext_lo16(u.w); v[8 * t + 7] = sext_hi16(u.w);
     }
   } else {
+    // the staged coefficient tile (packed r = 64: chunk t holds zig-zag positions 8 t .. 8 t + 7)
+    constexpr ZigZag zz = make_zigzag();
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       const int4 u = *(const int4*)(in + swz(lane, t));
-      v[8 * t + 0] = sext_lo16(u.x); v[8 * t + 1] = sext_hi16(u.x);
-      v[8 * t + 2] = sext_lo16(u.y); v[8 * t + 3] = sext_hi16(u.y);
-      v[8 * t + 4] = sext_lo16(u.z); v[8 * t + 5] = sext_hi16(u.z);
-      v[8 * t + 6] = sext_lo16(u.w); v[8 * t + 7] = sext_hi16(u.w);
+      const int32_t e[8] = {sext_lo16(u.x), sext_hi16(u.x), sext_lo16(u.y), sext_hi16(u.y),
+                            sext_lo16(u.z), sext_hi16(u.z), sext_lo16(u.w), sext_hi16(u.w)};
+#pragma unroll
+      for (int m = 0; m < 8; ++m) v[ZS == kZoneZZ64 ? zz.pos[8 * t + m] : 8 * t + m] = e[m];
     }
   }
 
   // ---- packed zonal output: the first r zig-zag coefficients, staged per lane ----
-  if (QMODE == QM_ZONAL_ZZ && KT::write_coef) {
+  if (QMODE == QM_ZONAL_ZZ && KT::write_coef && ZS == kZoneZZ64) {
+    // r = 64: eight 16-byte chunks of eight zig-zag positions each, staged
+    // like dense rows (or stored directly)
+    constexpr ZigZag zz = make_zigzag();
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      int32_t zq[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int k = zz.pos[8 * t + m];
+        zq[m] = v[k] + ((KT::in_pix && k == 0) ? -8192 : 0);  // the true coefficient
+      }
+      const int4 u = make_int4((int)pack16(zq[0], zq[1]), (int)pack16(zq[2], zq[3]), (int)pack16(zq[4], zq[5]),
+                               (int)pack16(zq[6], zq[7]));
+      if (stage_coef) *(int4*)(stage_out + swz(lane, t)) = u;
+      else __stcs((int4*)coef_of(d, pos, ch) + t, u);
+    }
+  } else if (QMODE == QM_ZONAL_ZZ && KT::write_coef) {
     constexpr ZigZag zz = make_zigzag();
     int16_t* out = stage_coef ? (int16_t*)stage_out + lane * zz_stride(qp.r) : coef_of_zz(d, pos, qp.r, ch);
 #pragma unroll
@@ -626,7 +658,7 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
         int64_t chunk, int stage_coef, unsigned long long* __restrict__ sse, unsigned int* __restrict__ fault,
         const QuantParams qp) {
   using KT = KindTraits<KIND>;
-  using SP = SmemPlan<KIND, NCH>;
+  using SP = SmemPlan<KIND, NCH, ZS>;
   constexpr int S = SP::stages;
   extern __shared__ __align__(128) uint8_t smem[];
   const int lane = threadIdx.x & 31;
@@ -699,7 +731,7 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
             if (!EDGE || k < nchunk) cp_async8(sa + ((i * 32 + lane) * NCH + k) * 8, row + 8 * k);
         }
       }
-    } else if (QMODE != QM_ZONAL_ZZ && NCH == 1) {
+    } else if ((QMODE != QM_ZONAL_ZZ || ZS == kZoneZZ64) && NCH == 1) {
       // Coefficients: lane copies 16-byte chunk c of block b (512 contiguous
       // bytes per warp instruction when the tile lies in one plane).
       const int16_t* mine = q.plane >= 0 ? coef_of(planes + q.plane, q) : nullptr;
@@ -763,7 +795,8 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
       }
       if (KT::write_coef && stage_coef) {
         __syncwarp();
-        if (QMODE == QM_ZONAL_ZZ) write_back_zz<zone_count(ZS)>(stage_out, planes, pc, lane, qp.r, zz_mh, ch);
+        if (QMODE == QM_ZONAL_ZZ && ZS != kZoneZZ64)
+          write_back_zz<zone_count(ZS)>(stage_out, planes, pc, lane, qp.r, zz_mh, ch);
         else write_back(stage_out, planes, pc, lane, ch);
         __syncwarp();
       }

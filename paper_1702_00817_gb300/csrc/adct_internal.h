@@ -23,7 +23,7 @@ enum Kind {
 struct LaunchShape {
   int threads;      // per CTA, multiple of 32, at most 256
   int ctas_per_sm;  // persistent grid = SMs x ctas_per_sm (at most)
-  int stage_coef;   // 0: direct 16-byte coefficient stores, 1: staged 512-byte warp stores
+  int stage_coef;   // 0: direct 16-byte coefficient stores, 1: staged 512-byte warp stores, -1: per kernel
 };
 
 struct CodecLaunch {
@@ -73,7 +73,7 @@ cudaError_t launch_codec(const CodecLaunch& c, const LaunchShape& shape, int sm_
 
 // Largest grid the persistent kernel uses for this shape (CTAs), and its dynamic shared memory.
 int codec_grid(const LaunchShape& shape, int sm_count, int64_t total);
-size_t codec_smem_bytes(const LaunchShape& shape, int kind, int nch = 1);
+size_t codec_smem_bytes(const LaunchShape& shape, int kind, int nch = 1, int zs = 14);
 
 // Exact-DCT comparator of the quality sweep: zonal round trip of every block
 // with the orthonormal 8x8 DCT-II in float32; per-plane squared error.

@@ -333,10 +333,13 @@ def test_autotune_keeps_results(codec):
 def test_launch_shape_automatic_default():
     c = Codec(0)
     assert c.get_launch()["ctas_per_sm"] == 0  # chosen per kernel by the library
+    assert c.get_launch()["stage_coef"] == -1  # staging chosen per call by the library
     c.set_launch(64, 5, 0)
     assert c.get_launch() == {"threads_per_cta": 64, "ctas_per_sm": 5, "stage_coef": 0, "reserved": 0}
     c.set_launch(128, -1, 1)
-    assert c.get_launch()["ctas_per_sm"] == 0
+    assert c.get_launch()["ctas_per_sm"] == 0 and c.get_launch()["stage_coef"] == 1
+    c.set_launch(0, 0, -1)
+    assert c.get_launch()["stage_coef"] == -1
     c.close()
 
 
