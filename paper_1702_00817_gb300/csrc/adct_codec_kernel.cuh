@@ -705,7 +705,38 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
   // warp's copies of one row cover 256 NCH contiguous bytes.
   auto issue = [&](int st, const Pos& q) {
     const uint32_t sa = smem_addr(wsm + st * SP::in_stage);
-    if (KT::in_pix) {
+    if (KT::in_pix && NCH > 1 && !EDGE) {
+      // Interleaved tile without edge blocks: lane l copies 8-byte chunk
+      // 32 k + l of every row of the tile (position (32 k + l) / NCH, part
+      // (32 k + l) % NCH), taking that position's row address from its lane,
+      // so each warp copy instruction reads 256 contiguous bytes when the
+      // positions are consecutive (each lane copying its own 8 NCH bytes
+      // touched 8 NCH partly used 32-byte sectors per instruction).  The
+      // stage layout is the same.
+      const uint8_t* mine = nullptr;
+      int64_t mpitch = 0;
+      if (q.plane >= 0) {
+        const PlaneDesc* d = planes + q.plane;
+        mpitch = __ldg(&d->pitch);
+        mine = src_of(d) + (int64_t)(8 * q.by) * mpitch + 8 * NCH * q.bx;
+#ifdef ADCT_CHECKED
+        if (8 * NCH * ((int64_t)__ldg(&d->bx0) + q.bx) + 8 * NCH > mpitch) {  // a copy would pass the end of the row
+          if (fault) atomicOr(fault, FAULT_ROW_BYTES);
+          mine = nullptr;
+        }
+#endif
+      }
+#pragma unroll
+      for (int k = 0; k < NCH; ++k) {
+        const int c = 32 * k + lane, p = c / NCH, part = c - p * NCH;
+        const uint8_t* b = (const uint8_t*)__shfl_sync(0xffffffffu, (unsigned long long)mine, p);
+        const int64_t pt = __shfl_sync(0xffffffffu, mpitch, p);
+        if (b) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) cp_async8(sa + (i * 32 * NCH + c) * 8, b + 8 * part + (int64_t)i * pt);
+        }
+      }
+    } else if (KT::in_pix) {
       if (q.plane >= 0) {
         const PlaneDesc* d = planes + q.plane;
         const int64_t pitch = __ldg(&d->pitch);

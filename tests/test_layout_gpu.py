@@ -120,7 +120,10 @@ def _check(codec, imgs, mode, s, r, with_coef=True, with_dst=True):
     return coefs
 
 
-EDGE_SIZES = [(1, 1), (7, 13), (9, 17), (15, 8), (8, 15), (100, 61), (37, 250), (64, 64)]
+# (100, 61), (37, 250), (75, 93): interior and both edge strips in separate launches;
+# (72, 93): right strip only; (75, 96): bottom strip only; the small ones stay whole
+EDGE_SIZES = [(1, 1), (7, 13), (9, 17), (15, 8), (8, 15), (100, 61), (37, 250), (64, 64), (75, 93), (72, 93),
+              (75, 96)]
 
 
 @pytest.mark.parametrize("mode,s,r", QUANTS)
@@ -132,7 +135,7 @@ def test_edge_extension_planar(codec, mode, s, r):
 @pytest.mark.parametrize("channels", [3, 4])
 @pytest.mark.parametrize("mode,s,r", QUANTS)
 def test_interleaved(codec, channels, mode, s, r):
-    sizes = [(8, 8), (24, 40), (27, 45), (120, 256), (1, 9), (73, 31)]
+    sizes = [(8, 8), (24, 40), (27, 45), (120, 256), (1, 9), (73, 31), (75, 93), (72, 93), (75, 96)]
     imgs = [(np.moveaxis(inputs.synth_image(h, w, 40 + k, channels=channels), 0, -1).copy(), True)
             for k, (h, w) in enumerate(sizes)]
     _check(codec, imgs, mode, s, r)
@@ -156,7 +159,9 @@ def test_mixed_layouts_in_one_call(codec):
 def test_inverse_into_interleaved_and_edge_images(codec, mode, s, r):
     imgs = [(np.moveaxis(inputs.synth_image(45, 83, 7, channels=3), 0, -1).copy(), True),
             (np.moveaxis(inputs.synth_image(16, 16, 8, channels=4), 0, -1).copy(), True),
-            (inputs.synth_image(21, 35, 9, channels=2), False)]
+            (inputs.synth_image(21, 35, 9, channels=2), False),
+            (np.moveaxis(inputs.synth_image(75, 93, 10, channels=3), 0, -1).copy(), True),  # split
+            (inputs.synth_image(100, 61, 11, channels=1), False)]  # split
     coefs = _check(codec, imgs, mode, s, r, with_dst=False)
     q = _quant(mode, s, r)
     outs = []
