@@ -189,14 +189,16 @@ adct_status build_quant(adct_context* ctx, const adct_quant* q, bool pixel_input
   qp.r = uses_zonal(q->mode) ? q->r : 64;
   for (int k = 0; k < 64; ++k) {
     const int i = k / 8, j = k % 8;
-    const int shift = 6 - scale_exp(i) - scale_exp(j);
+    // weights carry a factor 4 (2 extra shift bits): the kernels' pixel is the
+    // high byte of the saturated 16-bit 4 (R + 8224)
+    const int shift = 8 - scale_exp(i) - scale_exp(j);
     const int32_t zoff = (pixel_input && k == 0) ? -8192 : 0;
     qp.keep[k] = (!uses_zonal(q->mode) || rank[k] < q->r) ? -1 : 0;
     qp.c[k] = 0;
     qp.magic[k] = 0;
     qp.K[k] = 0;
     qp.ssel[k] = 0x4444u;
-    const int32_t bias = (k == 0) ? 8224 : 0;  // 32 + 128 * 64
+    const int32_t bias = (k == 0) ? 4 * 8224 : 0;  // 4 (32 + 128 * 64)
     if (!uses_step(q->mode)) {
       qp.w[k] = 1 << shift;
       qp.kw[k] = bias;

@@ -35,10 +35,10 @@
 //            added by the last butterfly stage), m = umulhi(n, magic) = floor(n / Q),
 //            q = m - K; for tables with even steps the sign of Z moves the bias by
 //            one so that ties round away from zero;
-//   dequant  S = q w, w = Q 2^(6 - a_i - a_j) (D^2 merged), + 8224 at (0, 0)
+//   dequant  S = q w, w = 4 Q 2^(6 - a_i - a_j) (D^2 merged), + 4 * 8224 at (0, 0)
 //            (rounding and level shift of every pixel: T^T e0 = 1);
 //   inverse  8 column then 8 row transposed butterflies;
-//   output   pixel = saturate_u8(R >> 6).
+//   output   pixel = high byte of saturate_u16(R), i.e. saturate_u8(R / 256).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -66,16 +66,19 @@ __device__ __forceinline__ int32_t sign_sel(int32_t x, uint32_t sel) {
   asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(0u), "r"(sel));
   return (int32_t)r;
 }
-// (c << 16) | (sat_u8(a) << 8) | sat_u8(b)
-__device__ __forceinline__ uint32_t cvt_pack_u8(int32_t a, int32_t b, uint32_t c) {
+// (sat_u16(a) << 16) | sat_u16(b)
+__device__ __forceinline__ uint32_t cvt_pack_u16(int32_t a, int32_t b) {
   uint32_t d;
-  asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  asm("cvt.pack.sat.u16.s32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
   return d;
 }
-// four reconstructed values (R + 8224) -> four saturated pixels, p0 in the lowest byte
+// Four reconstructed values 4 (R + 8224) -> four saturated pixels, p0 in the
+// lowest byte.  The dequantisation weights carry a factor 4, so that
+// pixel = clamp((R + 8224) >> 6, 0, 255) is the high byte of
+// clamp(4 (R + 8224), 0, 65535): two saturating packs of two values each and
+// one byte permute, instead of a shift per value and two packs.
 __device__ __forceinline__ uint32_t pixels4(int32_t r0, int32_t r1, int32_t r2, int32_t r3) {
-  const uint32_t hi = cvt_pack_u8(r3 >> 6, r2 >> 6, 0u);
-  return cvt_pack_u8(r1 >> 6, r0 >> 6, hi);
+  return __byte_perm(cvt_pack_u16(r1, r0), cvt_pack_u16(r3, r2), 0x7531);
 }
 
 // Bytes [0, n) of the little-endian 8-byte row r to p (8-byte aligned),
@@ -120,7 +123,7 @@ __device__ __forceinline__ int swz(int b, int c) { return b * 128 + ((c ^ (b & 7
 
 // Reconstruction offset carried by S_00: 32 (rounding of R / 64) + 128 * 64
 // (level shift); T^T e0 = 1 spreads it to every pixel of the block.
-constexpr int32_t kDcBias = 32 + 128 * 64;
+constexpr int32_t kDcBias = 4 * (32 + 128 * 64);  // times the factor 4 of the weights
 
 template <int KIND>
 struct KindTraits {

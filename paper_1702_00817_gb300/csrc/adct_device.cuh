@@ -142,8 +142,9 @@ static_assert(sizeof(PlaneDesc) == 64, "descriptor layout");
 //   STEP (Q > 16384): |Z| <= 8192 < Q/2, so q = 0: magic = c = K = 0.
 //   When Z is computed from raw pixels, Z_00 carries +8192 (the level shift
 //   T (X - 128) T^T = T X T^T - 8192 e0 e0^T); c at (0, 0) then includes -8192.
-//   w  : dequantisation weight Q * 2^(6 - a_i - a_j) (D^2 merged), Q = 1 unless STEP;
-//   kw : -K * w, plus 8224 = 32 + 128 * 64 at (0, 0), so that S = m * w + kw
+//   w  : dequantisation weight 4 * Q * 2^(6 - a_i - a_j) (D^2 merged; the factor 4
+//        puts the pixel in the high byte of a 16-bit value), Q = 1 unless STEP;
+//   kw : -K * w, plus 4 * 8224 (8224 = 32 + 128 * 64) at (0, 0), so that S = m * w + kw
 //        (8224: rounding of R / 64 and level shift of every pixel, T^T e0 = 1).
 //   keep: -1 where the zig-zag rank is below r, 0 elsewhere (ZONAL modes).
 struct QuantParams {
