@@ -105,8 +105,19 @@ int codec_grid(const LaunchShape& shape, int sm_count, int64_t total) {
   return (int)(want < 1 ? 1 : want);
 }
 
-cudaError_t launch_codec(const CodecLaunch& c, const LaunchShape& shape, int sm_count, cudaStream_t stream) {
-  if (c.total <= 0) return cudaSuccess;
+namespace {
+// One launch of the persistent kernel, resolved: the instantiation, its
+// resident grid and shared memory, and the coefficient staging.
+struct Prepared {
+  KernelFn fn = nullptr;
+  int grid = 0;     // CTAs (never more than can be resident at once)
+  int cap = 0;      // CTAs that can be resident at once
+  int threads = 0;
+  size_t smem = 0;
+  int stage = 1;
+};
+
+cudaError_t prepare_codec(const CodecLaunch& c, const LaunchShape& shape, int sm_count, Prepared& p) {
   KernelFn fn = nullptr;
   int zs = 14;  // zone of the kernel picked (its shared-memory plan)
   if (c.nch == 3 || c.nch == 4) {
@@ -144,18 +155,36 @@ cudaError_t launch_codec(const CodecLaunch& c, const LaunchShape& shape, int sm_
   LaunchShape sh = shape;
   if (sh.ctas_per_sm == 0) sh.ctas_per_sm = default_ctas_per_sm(c.kind, c.qmode);
   if (sh.ctas_per_sm > resident) sh.ctas_per_sm = resident;
-  const int grid = codec_grid(sh, sm_count, c.total);
-  const int64_t warps = (int64_t)grid * (shape.threads / 32);
-  int64_t chunk = (c.total + warps - 1) / warps;
-  chunk = (chunk + kTile - 1) / kTile * kTile;
+  p.fn = fn;
+  p.grid = codec_grid(sh, sm_count, c.total);
+  p.cap = sh.ctas_per_sm * sm_count;
+  p.threads = shape.threads;
+  p.smem = smem;
   // staging of the coefficients: the caller's choice, else staged except for
   // the packed round trip with r <= 8, whose direct stores measured faster
   // (r = 1: 185 us against 196 us staged; r = 10: 225 us against 211 us)
-  const int stage = shape.stage_coef >= 0 ? shape.stage_coef
-                                          : (c.qmode == QM_ZONAL_ZZ && c.kind == K_RT_FULL && c.qp.r <= 8) ? 0 : 1;
-  fn<<<grid, shape.threads, smem, stream>>>(c.planes, c.starts, c.nplanes, c.total, chunk, stage, c.sse, c.fault,
+  p.stage = shape.stage_coef >= 0 ? shape.stage_coef
+                                  : (c.qmode == QM_ZONAL_ZZ && c.kind == K_RT_FULL && c.qp.r <= 8) ? 0 : 1;
+  return cudaSuccess;
+}
+
+// Launches a prepared kernel on `grid` CTAs: each warp takes a contiguous
+// chunk of the flat block index, a whole number of 32-block tiles.
+cudaError_t fire(const CodecLaunch& c, const Prepared& p, int grid, cudaStream_t stream) {
+  const int64_t warps = (int64_t)grid * (p.threads / 32);
+  int64_t chunk = (c.total + warps - 1) / warps;
+  chunk = (chunk + kTile - 1) / kTile * kTile;
+  p.fn<<<grid, p.threads, p.smem, stream>>>(c.planes, c.starts, c.nplanes, c.total, chunk, p.stage, c.sse, c.fault,
                                             c.qp);
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_codec(const CodecLaunch& c, const LaunchShape& shape, int sm_count, cudaStream_t stream) {
+  if (c.total <= 0) return cudaSuccess;
+  Prepared p;
+  const cudaError_t e = prepare_codec(c, shape, sm_count, p);
+  return e != cudaSuccess ? e : fire(c, p, p.grid, stream);
 }
 
 }  // namespace adct

@@ -314,6 +314,77 @@ __device__ __forceinline__ void deinterleave_tile(uint8_t* stage, int lane) {
     }
 }
 
+// Byte selectors that take channel c's bytes out of an interleaved row span
+// (byte b of the span is pixel b / NCH, channel b % NCH): they depend on c
+// only, so one channel loop serves every channel.  NCH = 3: pixels 0-3 of
+// channel c are span bytes c, c + 3, c + 6, c + 9 in words 0-2, gathered by
+// one permute of words 0 and 1 (selector a; its third byte is overwritten
+// when c = 2) and one with word 2 (selector b); pixels 4-7 the same from words
+// 3-5.  NCH = 4: pixel j of channel c is byte c of word j; a takes it from
+// two words at once and b joins two such pairs.
+struct ChanSel {
+  uint32_t a, b;
+};
+template <int NCH>
+__device__ __forceinline__ ChanSel chan_sel(int c) {
+  if (NCH == 3) return {0x0630u + 0x0111u * (uint32_t)c, c == 2 ? 0x7410u : 0x5210u + 0x1000u * (uint32_t)c};
+  return {0x40u + 0x11u * (uint32_t)c, 0x5410u};
+}
+// Channel c's 8 bytes of one row (span words w[0 .. 2 NCH)) as pixels 0-3, 4-7.
+template <int NCH>
+__device__ __forceinline__ uint2 chan_row(const uint32_t* w, ChanSel k) {
+  if (NCH == 3)
+    return make_uint2(__byte_perm(__byte_perm(w[0], w[1], k.a), w[2], k.b),
+                      __byte_perm(__byte_perm(w[3], w[4], k.a), w[5], k.b));
+  return make_uint2(__byte_perm(__byte_perm(w[0], w[1], k.a), __byte_perm(w[2], w[3], k.a), k.b),
+                    __byte_perm(__byte_perm(w[4], w[5], k.a), __byte_perm(w[6], w[7], k.a), k.b));
+}
+
+// Edge blocks: byte j of each row becomes byte min(j, vc - 1), one byte
+// permute per 4 bytes (selector nibble j = min(j, vc - 1); the identity for
+// full blocks).
+__device__ __forceinline__ uint32_t edge_fill_sel(int vc) {
+  const uint32_t c = (uint32_t)vc - 1u;
+  const uint32_t hi = c >= 7u ? 0u : 0xFFFFFFFFu << (4u * (c + 1u));  // nibbles above c
+  return (0x76543210u & ~hi) | (c * 0x11111111u & hi);
+}
+
+// Raw pixels of row w (bytes 0-7) into v[8 i .. 8 i + 7], after the edge fill.
+template <bool EDGE>
+__device__ __forceinline__ void unpack_row(uint2 w, uint32_t sel, int i, int32_t (&v)[64]) {
+  if (EDGE) {
+    const uint2 raw = w;
+    w.x = __byte_perm(raw.x, raw.y, sel & 0xFFFFu);
+    w.y = __byte_perm(raw.x, raw.y, sel >> 16);
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    v[8 * i + j] = (int32_t)__byte_perm(w.x, 0u, 0x4440 | j);
+    v[8 * i + 4 + j] = (int32_t)__byte_perm(w.y, 0u, 0x4440 | j);
+  }
+}
+
+// Interleaved input read per channel: channel ch of lane's block straight from
+// the tile's interleaved stage (its 8 NCH-byte row spans), unpacked into v.
+template <int NCH, bool EDGE>
+__device__ __forceinline__ void read_interleaved(const uint8_t* __restrict__ in, const PlaneDesc* __restrict__ planes,
+                                                 const Pos& pos, int ch, int lane, int32_t (&v)[64]) {
+  const ChanSel k = chan_sel<NCH>(ch);
+  const uint32_t sel = EDGE ? edge_fill_sel(valid_cols(planes + pos.plane, pos)) : 0x76543210u;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const uint2* sp = (const uint2*)(in + (i * 32 + lane) * 8 * NCH);
+    uint32_t w[2 * NCH];
+#pragma unroll
+    for (int t = 0; t < NCH; ++t) {
+      const uint2 u = sp[t];
+      w[2 * t] = u.x;
+      w[2 * t + 1] = u.y;
+    }
+    unpack_row<EDGE>(chan_row<NCH>(w, k), sel, i, v);
+  }
+}
+
 // Arithmetic of one 8x8 block: read its input from the input stage, quantise,
 // stage or store q, dequantise, invert and store the pixels.
 //
@@ -324,10 +395,14 @@ __device__ __forceinline__ void deinterleave_tile(uint8_t* stage, int lane) {
 // EDGE: the launch may contain blocks on the right or bottom edge of an image
 // whose side is not a multiple of 8 (compiled out of the launches that have
 // none).
-template <int KIND, int QMODE, bool EVENQ, int ZS, int NCH, bool EDGE>
-__device__ __forceinline__ uint32_t block_step(uint8_t* __restrict__ in, uint8_t* __restrict__ stage_out,
-                                               const PlaneDesc* __restrict__ planes, const Pos& pos, int ch,
-                                               int stage_coef, const QuantParams& qp, int lane) {
+//
+// PRE: v already holds the block's raw pixels (read_interleaved); its
+// reconstruction goes to channel ch's planar tile in `recon` instead of `in`.
+template <int KIND, int QMODE, bool EVENQ, int ZS, int NCH, bool EDGE, bool PRE = false>
+__device__ __forceinline__ uint32_t block_step(int32_t (&v)[64], uint8_t* __restrict__ in, uint8_t* recon,
+                                               uint8_t* __restrict__ stage_out, const PlaneDesc* __restrict__ planes,
+                                               const Pos& pos, int ch, int stage_coef, const QuantParams& qp,
+                                               int lane) {
   using KT = KindTraits<KIND>;
   // With a zonal quantiser every coefficient beyond anti-diagonal ZS is zero
   // (the kept r fit in diagonals 0..ZS): known at compile time, so the forward
@@ -339,31 +414,12 @@ __device__ __forceinline__ uint32_t block_step(uint8_t* __restrict__ in, uint8_t
   // valid columns / rows (edge blocks: the rest replicates the last valid one;
   // the input stage already holds the last valid row in place of the others)
   const int vc = EDGE ? valid_cols(d, pos) : 8, vr = EDGE ? valid_rows(d, pos) : 8;
-  int32_t v[64];
   if (KT::in_pix) {
-    const uint2* st = (const uint2*)(in + (NCH > 1 ? ch * 2048 : 0));
-    // Edge blocks: byte j of each row becomes byte min(j, vc - 1), one byte
-    // permute per 4 bytes (selector nibble j = min(j, vc - 1); the identity
-    // for full blocks).
-    uint32_t sel = 0x76543210u;
-    if (EDGE) {
-      const uint32_t c = (uint32_t)vc - 1u;
-      const uint32_t hi = c >= 7u ? 0u : 0xFFFFFFFFu << (4u * (c + 1u));  // nibbles above c
-      sel = (sel & ~hi) | (c * 0x11111111u & hi);
-    }
+    if (!PRE) {
+      const uint2* st = (const uint2*)(in + (NCH > 1 ? ch * 2048 : 0));
+      const uint32_t sel = EDGE ? edge_fill_sel(vc) : 0x76543210u;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      uint2 w = st[i * 32 + lane];
-      if (EDGE) {
-        const uint2 raw = w;
-        w.x = __byte_perm(raw.x, raw.y, sel & 0xFFFFu);
-        w.y = __byte_perm(raw.x, raw.y, sel >> 16);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        v[8 * i + j] = (int32_t)__byte_perm(w.x, 0u, 0x4440 | j);
-        v[8 * i + 4 + j] = (int32_t)__byte_perm(w.y, 0u, 0x4440 | j);
-      }
+      for (int i = 0; i < 8; ++i) unpack_row<EDGE>(st[i * 32 + lane], sel, i, v);
     }
     fwd2d(v);  // Z + 8192 e0 e0^T (raw pixels; the level shift lives in the constants)
   } else if (QMODE == QM_ZONAL_ZZ && ZS != kZoneZZ64) {
@@ -519,7 +575,7 @@ __device__ __forceinline__ uint32_t block_step(uint8_t* __restrict__ in, uint8_t
       // interleaved: the reconstructed rows back into this channel's planar
       // tile (its input is consumed), interleaved and stored once every
       // channel is done
-      uint2* pl = (uint2*)(in + ch * 2048);
+      uint2* pl = (uint2*)((PRE ? recon : in) + ch * 2048);
 #pragma unroll
       for (int i = 0; i < 8; ++i)
         pl[i * 32 + lane] = make_uint2(pixels4(v[8 * i + 0], v[8 * i + 1], v[8 * i + 2], v[8 * i + 3]),
@@ -663,6 +719,15 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
   using KT = KindTraits<KIND>;
   using SP = SmemPlan<KIND, NCH, ZS>;
   constexpr int S = SP::stages;
+  // Interleaved pixel input of the step-quantised kinds that reconstruct
+  // pixels (not the squared-error kind): one input stage, read per channel
+  // (read_interleaved) and refilled with the next tile once the last channel
+  // has read it; the second stage holds the channels' reconstructed planar
+  // tiles.  The other kinds and modes keep the in-place de-interleave:
+  // issuing the next tile's copies while a block is live in registers made
+  // them spill.
+  constexpr bool kLazy = NCH > 1 && KT::in_pix && KT::inv && !KT::sse && (QMODE == QM_STEP || QMODE == QM_STEP_ZONAL);
+  static_assert(!kLazy || S == 2, "the interleaved pipeline uses two stages");
   extern __shared__ __align__(128) uint8_t smem[];
   const int lane = threadIdx.x & 31;
   uint8_t* wsm = smem + (threadIdx.x >> 5) * SP::warp;
@@ -804,13 +869,18 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
   for (int32_t base = 0; base < rend; base += kTile) {
     __syncwarp();  // every lane is done reading tile i - 1's stage, refilled now
     const Pos pl = checked(cur.locate(planes, starts, begin, base + kTile * (S - 1) + lane, rend));
-    issue(s == 0 ? S - 1 : s - 1, pl);
-    cp_async_wait<S - 1>();
+    if (!kLazy) {
+      issue(s == 0 ? S - 1 : s - 1, pl);
+      cp_async_wait<S - 1>();
+    } else {
+      cp_async_wait<0>();
+    }
     __syncwarp();
 
     const Pos pc = ring[0];
     uint8_t* stage = wsm + s * SP::in_stage;
-    if (NCH > 1 && KT::in_pix) {
+    uint8_t* recon = kLazy ? wsm + SP::in_stage : stage;  // reconstructed planar tiles
+    if (NCH > 1 && KT::in_pix && !kLazy) {
       deinterleave_tile<NCH>(stage, lane);
       __syncwarp();
     }
@@ -819,8 +889,16 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
       acc_plane = pc.plane;
     }
     auto channel = [&](int ch) {
-      const uint32_t e =
-          block_step<KIND, QMODE, EVENQ, ZS, NCH, EDGE>(stage, stage_out, planes, pc, ch, stage_coef, qp, lane);
+      int32_t v[64];
+      if (kLazy) {
+        if (pc.plane >= 0) read_interleaved<NCH, EDGE>(stage, planes, pc, ch, lane, v);
+        if (ch == NCH - 1) {  // every channel's input is read: the stage takes the next tile
+          __syncwarp();
+          issue(0, pl);
+        }
+      }
+      const uint32_t e = block_step<KIND, QMODE, EVENQ, ZS, NCH, EDGE, kLazy>(v, stage, recon, stage_out, planes, pc,
+                                                                            ch, stage_coef, qp, lane);
       if (KT::sse) {
         if (ch == 0) acc0 += e;
         else if (ch == 1) acc1 += e;
@@ -841,11 +919,11 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
 #pragma unroll 1
       for (int ch = 0; ch < NCH; ++ch) channel(ch);
     }
-    if (NCH > 1 && KT::inv && !KT::sse) write_pixels_interleaved<NCH, EDGE>(stage, planes, pc, lane);
+    if (NCH > 1 && KT::inv && !KT::sse) write_pixels_interleaved<NCH, EDGE>(recon, planes, pc, lane);
 #pragma unroll
     for (int k = 0; k + 1 < S - 1; ++k) ring[k] = ring[k + 1];
     ring[S - 2] = pl;
-    if (++s == S) s = 0;
+    if (!kLazy && ++s == S) s = 0;
   }
   if (KT::sse) flush();
   cp_async_wait<0>();
