@@ -127,14 +127,17 @@ typedef struct {
 
 /*
  * Launch shape of the integer kernels (one 8x8 block per thread, each warp a
- * tile of 32 blocks, up to 12.4 KB of shared memory per warp).  Zero fields of
+ * tile of 32 blocks, up to 16.5 KB of shared memory per warp).  Zero fields of
  * threads_per_cta / ctas_per_sm keep the current value.
  *   threads_per_cta   multiple of 32 in [32, 128] (default 128)
  *   ctas_per_sm       CTAs per SM the persistent grid is sized for (1..32); capped
  *                     at the number that can be resident at once.  A negative
  *                     value (and a new context) leaves the choice to the
  *                     library, per kernel: 4, or 3 for the encode with dense
- *                     coefficient output; adct_get_launch then reports 0
+ *                     coefficient output; adct_get_launch then reports 0.
+ *                     In that mode the launches for channel-interleaved images
+ *                     use CTAs of 32 threads, 12 per SM, whatever
+ *                     threads_per_cta says
  *   stage_coef        0: each thread stores its 128 coefficient bytes directly;
  *                     1: coefficients are staged through shared memory and
  *                        written by the warp as contiguous 512-byte stores;

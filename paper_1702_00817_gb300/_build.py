@@ -13,7 +13,8 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libadct.so")
 LIB_CHECKED = os.path.join(PKG, "libadct_checked.so")  # kernels with bounds checks (ADCT_CHECKED)
 SOURCES = ["adct_api.cu", "adct_codec.cu", "adct_codec_zonal_lo.cu", "adct_codec_zonal_hi.cu",
-           "adct_codec_interleaved.cu", "adct_codec_interleaved_edge.cu", "adct_codec_edge.cu", "adct_float.cu",
+           "adct_codec_interleaved.cu", "adct_codec_interleaved_edge.cu", "adct_codec_edge.cu", "adct_codec_masked.cu",
+           "adct_codec_interleaved_masked.cu", "adct_float.cu",
            "adct_quality.cu", "adct_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -249,6 +249,10 @@ adct_status check_image(const adct_image& im, int need, bool coef_only, const ch
   return ADCT_OK;
 }
 
+// Launch groups of a call without split images: planar, 3-channel and
+// 4-channel interleaved, each without and with edge blocks (group_of).
+constexpr int kGroups = 6;
+
 // Appends image im's descriptors (one per planar plane, or one for an
 // interleaved image) to out[*count..]; cpb is the number of int16
 // coefficients stored per block (64, or r when packed); plane_id numbers
@@ -299,8 +303,9 @@ int describe_image(const adct_image& im, int32_t cpb, bool coef_only, int32_t pl
 // Descriptors of one planar plane or one interleaved image (`one`: channels
 // 1, or an interleaved image), split when it has edge blocks and at least
 // kSplitMin interior blocks: the interior (every block with 8 x 8 valid
-// pixels) goes to the group without edge handling, the last block column and
-// the rest of the last block row to the edge group; otherwise one descriptor.
+// pixels; its flat rows include the masked last column) goes to the group
+// without edge handling, the last block column and the rest of the last block
+// row to the edge group; otherwise one descriptor.
 // Returns the count (1..3); part k belongs to group groups[k].
 constexpr int64_t kSplitMin = 64;
 int describe_parts(const adct_image& one, int32_t cpb, bool coef_only, int32_t plane_id, PlaneDesc parts[3],
@@ -315,13 +320,17 @@ int describe_parts(const adct_image& one, int32_t cpb, bool coef_only, int32_t p
   const int64_t bpx = 8 * (int64_t)whole.nch;  // pixel bytes of a block row segment
   const int64_t cpb64 = cpb;
   int n = 0;
-  PlaneDesc d = whole;  // the interior
-  d.wb = wi;
+  // The interior.  With a right edge column its flat rows still span the
+  // whole coefficient row, so that the 32-block tiles stay aligned with the
+  // image's rows; the last column is masked (ew = 0: the kernels without edge
+  // handling skip it) and goes to the edge launch.
+  PlaneDesc d = whole;
+  d.wb = whole.wb;
   d.hb = hi;
-  d.ew = 8;
+  d.ew = right ? 0 : 8;
   d.eh = 8;
   parts[n] = d;
-  groups[n++] = g & ~1;
+  groups[n++] = right ? kGroups + (g >> 1) : (g & ~1);  // masked interior, or the group without edges
   if (right) {  // the last block column, every block row
     d = whole;
     d.src = whole.src ? whole.src + bpx * (whole.wb - 1) : nullptr;
@@ -348,32 +357,37 @@ int describe_parts(const adct_image& one, int32_t cpb, bool coef_only, int32_t p
 
 // Work units of one call: one group (one launch) per pixel layout class;
 // images with edge blocks get their own launch so that the others run kernels
-// with the edge handling compiled out.
-constexpr int kGroups = 6;
-constexpr int kGroupNch[kGroups] = {1, 1, 3, 3, 4, 4};
-constexpr bool kGroupEdge[kGroups] = {false, true, false, true, false, true};
+// with the edge handling compiled out.  After the kGroups groups come three
+// more for the interiors of split images with a right edge column (planar, 3
+// and 4 channels), whose last block column is masked (kernel edge class
+// kEdgeMasked).
+constexpr int kGroupsAll = kGroups + 3;
+constexpr int kGroupNch[kGroupsAll] = {1, 1, 3, 3, 4, 4, 1, 3, 4};
+constexpr bool kGroupEdge[kGroupsAll] = {false, true, false, true, false, true, false, false, false};
+constexpr int kGroupClass[kGroupsAll] = {kEdgeNone, kEdgeBlocks, kEdgeNone,   kEdgeBlocks, kEdgeNone,
+                                         kEdgeBlocks, kEdgeMasked, kEdgeMasked, kEdgeMasked};
 
 int64_t blocks_of(const adct_image& im) { return (int64_t)((im.width + 7) / 8) * ((im.height + 7) / 8); }
 
 struct Tables {
-  std::vector<PlaneDesc> planes[kGroups];
-  std::vector<int64_t> starts[kGroups];  // flat-index prefix per group (nplanes + 1)
+  std::vector<PlaneDesc> planes[kGroupsAll];
+  std::vector<int64_t> starts[kGroupsAll];  // flat-index prefix per group (nplanes + 1)
   int32_t nplanes = 0;                   // planes of the call (per-plane outputs)
   int64_t blocks = 0;                    // 8x8 blocks of the call, all channels
   std::vector<uint8_t> blob;             // the groups' tables back to back, as uploaded
-  size_t off_planes[kGroups], off_starts[kGroups];
+  size_t off_planes[kGroupsAll], off_starts[kGroupsAll];
 
   int64_t total(int g) const { return starts[g].empty() ? 0 : starts[g].back(); }
   void serialise() {
     size_t off = 0;
-    for (int g = 0; g < kGroups; ++g) {
+    for (int g = 0; g < kGroupsAll; ++g) {
       off_planes[g] = off;
       off += planes[g].size() * sizeof(PlaneDesc);
       off_starts[g] = off;
       off += starts[g].size() * sizeof(int64_t);
     }
     blob.resize(off);
-    for (int g = 0; g < kGroups; ++g) {
+    for (int g = 0; g < kGroupsAll; ++g) {
       if (!planes[g].empty()) std::memcpy(blob.data() + off_planes[g], planes[g].data(), planes[g].size() * sizeof(PlaneDesc));
       if (!starts[g].empty()) std::memcpy(blob.data() + off_starts[g], starts[g].data(), starts[g].size() * sizeof(int64_t));
     }
@@ -392,7 +406,7 @@ adct_status build_tables(adct_context* ctx, const adct_image* imgs, int32_t n, i
                          Tables& t) {
   if (n < 0) return fail(ctx, ADCT_ERR_INVALID_ARG, "negative image count");
   if (n > 0 && !imgs) return fail(ctx, ADCT_ERR_INVALID_ARG, "imgs is NULL");
-  for (int g = 0; g < kGroups; ++g) {
+  for (int g = 0; g < kGroupsAll; ++g) {
     t.planes[g].clear();
     t.starts[g].assign(1, 0);
   }
@@ -509,14 +523,14 @@ int need_for_kind(int kind) {
 // Launches every non-empty group of a call, one after the other on `stream`.
 adct_status launch_groups(adct_context* ctx, CodecLaunch cl, const Tables& t, const char* dev, const LaunchShape& shape,
                           cudaStream_t stream, bool timed = true) {
-  for (int g = 0; g < kGroups; ++g) {
+  for (int g = 0; g < kGroupsAll; ++g) {
     if (t.total(g) == 0) continue;
     cl.planes = (const PlaneDesc*)(dev + t.off_planes[g]);
     cl.starts = (const int64_t*)(dev + t.off_starts[g]);
     cl.nplanes = (int32_t)t.planes[g].size();
     cl.total = t.total(g);
     cl.nch = kGroupNch[g];
-    cl.edge = kGroupEdge[g];
+    cl.edge = kGroupClass[g];
     cudaError_t e;
     if (timed) {
       TimedLaunch tl(ctx, stream);

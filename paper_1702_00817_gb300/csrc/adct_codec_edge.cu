@@ -6,6 +6,6 @@
 
 namespace adct {
 
-KernelFn pick_edge_kernel(int kind, int qmode, bool evenq) { return pick_full<1, true>(kind, qmode, evenq); }
+KernelFn pick_edge_kernel(int kind, int qmode, bool evenq) { return pick_full<1, kEdgeBlocks>(kind, qmode, evenq); }
 
 }  // namespace adct

@@ -6,8 +6,8 @@
 namespace adct {
 
 KernelFn pick_interleaved_kernel(int kind, int qmode, bool evenq, int nch) {
-  if (nch == 3) return pick_full<3, false>(kind, qmode, evenq);
-  if (nch == 4) return pick_full<4, false>(kind, qmode, evenq);
+  if (nch == 3) return pick_full<3, kEdgeNone>(kind, qmode, evenq);
+  if (nch == 4) return pick_full<4, kEdgeNone>(kind, qmode, evenq);
   return nullptr;
 }
 

@@ -6,8 +6,8 @@
 namespace adct {
 
 KernelFn pick_interleaved_edge_kernel(int kind, int qmode, bool evenq, int nch) {
-  if (nch == 3) return pick_full<3, true>(kind, qmode, evenq);
-  if (nch == 4) return pick_full<4, true>(kind, qmode, evenq);
+  if (nch == 3) return pick_full<3, kEdgeBlocks>(kind, qmode, evenq);
+  if (nch == 4) return pick_full<4, kEdgeBlocks>(kind, qmode, evenq);
   return nullptr;
 }
 

@@ -187,6 +187,7 @@ struct Cursor {
   int32_t first, next_start;  // plane p spans [first, next_start) relative to the chunk start
   Pos last;                   // position returned by the previous call (plane < 0: none)
 
+  template <bool MASK>
   __device__ __forceinline__ Pos locate(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts,
                                         int64_t begin, int32_t r, int32_t rend) {
     Pos q;
@@ -215,6 +216,10 @@ struct Cursor {
       q.bx = f - q.by * wb;
     }
     last = q;
+    // MASK: a descriptor whose last block column belongs to another launch
+    // (the interior of an image with edge blocks, marked ew = 0: its flat rows
+    // span the whole coefficient row so that tiles stay aligned) skips it.
+    if (MASK && q.bx + 1 == wb && __ldg(&planes[p].ew) == 0) q.plane = -1;
     return q;
   }
 };
@@ -636,13 +641,18 @@ __device__ __forceinline__ void write_pixels_interleaved(const uint8_t* __restri
 // Write a staged 32-block half-tile of coefficients back with 512-byte warp
 // stores when the active lanes' blocks are consecutive in memory (one
 // contiguous range: the usual case; not when the tile crosses a plane, or a
-// block row of a descriptor narrower than its coefficient rows).
+// block row of a descriptor narrower than its coefficient rows).  MASKED
+// (interiors with a masked column): inactive lanes may sit anywhere in the
+// warp, not only past the end of the chunk; their blocks are left untouched.
+template <bool MASKED>
 __device__ __forceinline__ void write_back(const uint8_t* __restrict__ stage_out, const PlaneDesc* __restrict__ planes,
                                           const Pos& pos, int lane, int ch) {
   const bool active = pos.plane >= 0;
   const unsigned act = __ballot_sync(0xffffffffu, active);
+  if (MASKED && act == 0) return;
   int16_t* mine = active ? coef_of(planes + pos.plane, pos, ch) : nullptr;
-  int16_t* const base = (int16_t*)__shfl_sync(0xffffffffu, (unsigned long long)mine, 0);
+  const int f = MASKED ? __ffs(act) - 1 : 0;  // first active lane
+  int16_t* const base = (int16_t*)__shfl_sync(0xffffffffu, (unsigned long long)mine, f) - 64 * f;
   // Instruction k moves bytes [512 k, 512 k + 512) of the half-tile: lane l
   // takes 16-byte chunk (l & 7) of block 4 k + (l >> 3), i.e. byte 512 k + 16 l;
   // in shared memory that chunk sits at one of two lane-specific offsets (the
@@ -651,10 +661,11 @@ __device__ __forceinline__ void write_back(const uint8_t* __restrict__ stage_out
   const uint32_t rd0 = pb * 128 + ((pc ^ pb) << 4), rd1 = pb * 128 + ((pc ^ (pb + 4)) << 4);
   if (__all_sync(0xffffffffu, !active || mine == base + 64 * lane)) {
     int4* gp = (int4*)base + lane;
-    const int nact = __popc(act);  // active lanes are a prefix of the warp
+    const int nact = __popc(act);  // without MASKED the active lanes are a prefix of the warp
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      if (4 * k + pb < nact) __stcs(gp + 32 * k, *(const int4*)(stage_out + 512 * k + ((k & 1) ? rd1 : rd0)));
+      const bool wr = MASKED ? ((act >> (4 * k + pb)) & 1u) != 0 : 4 * k + pb < nact;
+      if (wr) __stcs(gp + 32 * k, *(const int4*)(stage_out + 512 * k + ((k & 1) ? rd1 : rd0)));
     }
   } else {
 #pragma unroll
@@ -674,7 +685,7 @@ __device__ __forceinline__ void write_back(const uint8_t* __restrict__ stage_out
 // own r.  With padding (r a multiple of 4) value e of the range sits at
 // e + 2 (e / r) in the staging, so word w at w + w / (r / 2); the division is a
 // multiply by mh = ceil(2^20 / (r / 2)), exact for w < 2^10.
-template <int NMAX>
+template <int NMAX, bool MASKED>
 __device__ __forceinline__ void write_back_zz(const uint8_t* __restrict__ stage_out,
                                              const PlaneDesc* __restrict__ planes, const Pos& pos, int lane, int r,
                                              uint32_t mh, int ch) {
@@ -684,7 +695,8 @@ __device__ __forceinline__ void write_back_zz(const uint8_t* __restrict__ stage_
   const int16_t* st16 = (const int16_t*)stage_out;
   const bool padded = (r & 3) == 0;
   int16_t* const base = (int16_t*)__shfl_sync(0xffffffffu, (unsigned long long)mine, 0);
-  if (__all_sync(0xffffffffu, !active || mine == base + r * lane)) {
+  const bool prefix = !MASKED || (act & (act + 1u)) == 0;  // active lanes are a prefix of the warp
+  if (prefix && __all_sync(0xffffffffu, !active || mine == base + r * lane)) {
     const int n = __popc(act) * r;  // values to write
     if (((uintptr_t)base & 3) == 0 && (n & 1) == 0) {
       constexpr int kWords = (NMAX + 1) / 2;  // words per lane at most (32 r / 2 / 32)
@@ -711,7 +723,7 @@ __device__ __forceinline__ void write_back_zz(const uint8_t* __restrict__ stage_
   }
 }
 
-template <int KIND, int QMODE, bool EVENQ, int ZS, int NCH = 1, bool EDGE = false>
+template <int KIND, int QMODE, bool EVENQ, int ZS, int NCH = 1, int EDGE = kEdgeNone>
 __global__ void __launch_bounds__(kMaxThreads, 3)
 k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts, int32_t nplanes, int64_t total,
         int64_t chunk, int stage_coef, unsigned long long* __restrict__ sse, unsigned int* __restrict__ fault,
@@ -719,6 +731,8 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
   using KT = KindTraits<KIND>;
   using SP = SmemPlan<KIND, NCH, ZS>;
   constexpr int S = SP::stages;
+  constexpr bool EB = EDGE == kEdgeBlocks;      // edge blocks: clamped copies, column fill, partial stores
+  constexpr bool MASKED = EDGE == kEdgeMasked;  // interiors whose last block column is masked
   // Interleaved pixel input of the step-quantised kinds that reconstruct
   // pixels (not the squared-error kind): one input stage, read per channel
   // (read_interleaved) and refilled with the next tile once the last channel
@@ -773,7 +787,7 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
   // warp's copies of one row cover 256 NCH contiguous bytes.
   auto issue = [&](int st, const Pos& q) {
     const uint32_t sa = smem_addr(wsm + st * SP::in_stage);
-    if (KT::in_pix && NCH > 1 && !EDGE) {
+    if (KT::in_pix && NCH > 1 && !EB) {
       // Interleaved tile without edge blocks: lane l copies 8-byte chunk
       // 32 k + l of every row of the tile (position (32 k + l) / NCH, part
       // (32 k + l) % NCH), taking that position's row address from its lane,
@@ -813,8 +827,8 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
         // only the 8-byte chunks that hold valid pixels (they end at or
         // before ceil8(width * NCH) <= pitch, inside the row); the missing
         // columns are filled from the last valid one when the block is read.
-        const int vc = EDGE ? valid_cols(d, q) : 8, vr = EDGE ? valid_rows(d, q) : 8;
-        const int nchunk = EDGE ? (NCH * vc + 7) / 8 : NCH;
+        const int vc = EB ? valid_cols(d, q) : 8, vr = EB ? valid_rows(d, q) : 8;
+        const int nchunk = EB ? (NCH * vc + 7) / 8 : NCH;
 #ifdef ADCT_CHECKED
         if (8 * NCH * ((int64_t)__ldg(&d->bx0) + q.bx) + 8 * nchunk > pitch) {  // a copy would pass the end of the row
           if (fault) atomicOr(fault, FAULT_ROW_BYTES);
@@ -824,10 +838,10 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
 #endif
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          const uint8_t* row = src + (int64_t)(EDGE ? min(i, vr - 1) : i) * pitch;
+          const uint8_t* row = src + (int64_t)(EB ? min(i, vr - 1) : i) * pitch;
 #pragma unroll
           for (int k = 0; k < NCH; ++k)
-            if (!EDGE || k < nchunk) cp_async8(sa + ((i * 32 + lane) * NCH + k) * 8, row + 8 * k);
+            if (!EB || k < nchunk) cp_async8(sa + ((i * 32 + lane) * NCH + k) * 8, row + 8 * k);
         }
       }
     } else if ((QMODE != QM_ZONAL_ZZ || ZS == kZoneZZ64) && NCH == 1) {
@@ -862,13 +876,13 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
   Pos ring[S - 1];  // positions of tiles i .. i + S - 2, whose copies are issued
 #pragma unroll
   for (int k = 0; k < S - 1; ++k) {
-    ring[k] = checked(cur.locate(planes, starts, begin, kTile * k + lane, rend));
+    ring[k] = checked(cur.template locate<MASKED>(planes, starts, begin, kTile * k + lane, rend));
     issue(k, ring[k]);
   }
   int s = 0;  // stage of tile i
   for (int32_t base = 0; base < rend; base += kTile) {
     __syncwarp();  // every lane is done reading tile i - 1's stage, refilled now
-    const Pos pl = checked(cur.locate(planes, starts, begin, base + kTile * (S - 1) + lane, rend));
+    const Pos pl = checked(cur.template locate<MASKED>(planes, starts, begin, base + kTile * (S - 1) + lane, rend));
     if (!kLazy) {
       issue(s == 0 ? S - 1 : s - 1, pl);
       cp_async_wait<S - 1>();
@@ -891,13 +905,13 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
     auto channel = [&](int ch) {
       int32_t v[64];
       if (kLazy) {
-        if (pc.plane >= 0) read_interleaved<NCH, EDGE>(stage, planes, pc, ch, lane, v);
+        if (pc.plane >= 0) read_interleaved<NCH, EB>(stage, planes, pc, ch, lane, v);
         if (ch == NCH - 1) {  // every channel's input is read: the stage takes the next tile
           __syncwarp();
           issue(0, pl);
         }
       }
-      const uint32_t e = block_step<KIND, QMODE, EVENQ, ZS, NCH, EDGE, kLazy>(v, stage, recon, stage_out, planes, pc,
+      const uint32_t e = block_step<KIND, QMODE, EVENQ, ZS, NCH, EB, kLazy>(v, stage, recon, stage_out, planes, pc,
                                                                             ch, stage_coef, qp, lane);
       if (KT::sse) {
         if (ch == 0) acc0 += e;
@@ -908,8 +922,8 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
       if (KT::write_coef && stage_coef) {
         __syncwarp();
         if (QMODE == QM_ZONAL_ZZ && ZS != kZoneZZ64)
-          write_back_zz<zone_count(ZS)>(stage_out, planes, pc, lane, qp.r, zz_mh, ch);
-        else write_back(stage_out, planes, pc, lane, ch);
+          write_back_zz<zone_count(ZS), MASKED>(stage_out, planes, pc, lane, qp.r, zz_mh, ch);
+        else write_back<MASKED>(stage_out, planes, pc, lane, ch);
         __syncwarp();
       }
     };
@@ -919,7 +933,7 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
 #pragma unroll 1
       for (int ch = 0; ch < NCH; ++ch) channel(ch);
     }
-    if (NCH > 1 && KT::inv && !KT::sse) write_pixels_interleaved<NCH, EDGE>(recon, planes, pc, lane);
+    if (NCH > 1 && KT::inv && !KT::sse) write_pixels_interleaved<NCH, EB>(recon, planes, pc, lane);
 #pragma unroll
     for (int k = 0; k + 1 < S - 1; ++k) ring[k] = ring[k + 1];
     ring[S - 2] = pl;
@@ -947,7 +961,7 @@ KernelFn pick_zone(int kind, int qmode) {
 // The full-zone kernels of one pixel layout / edge class (NCH channels per
 // descriptor, EDGE handling) for every kind that touches pixels; nullptr for
 // the coefficient-only quantiser.
-template <int KIND, int NCH, bool EDGE>
+template <int KIND, int NCH, int EDGE>
 KernelFn pick_full_mode(int qmode, bool evenq) {
   switch (qmode) {
     case QM_STEP:
@@ -963,7 +977,7 @@ KernelFn pick_full_mode(int qmode, bool evenq) {
   }
 }
 
-template <int NCH, bool EDGE>
+template <int NCH, int EDGE>
 KernelFn pick_full(int kind, int qmode, bool evenq) {
   switch (kind) {
     case K_FORWARD: return k_codec<K_FORWARD, QM_NONE, false, 14, NCH, EDGE>;

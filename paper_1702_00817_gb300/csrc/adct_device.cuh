@@ -121,7 +121,8 @@ struct PlaneDesc {
   int32_t hb;       // block rows of this descriptor
   int32_t cwb;      // blocks per coefficient row (the whole image's blocks per row)
   int32_t plane_id; // plane number of channel 0 in the call (per-plane outputs)
-  int16_t ew;       // valid pixel columns of the descriptor's last block column
+  int16_t ew;       // valid pixel columns of the descriptor's last block column (0: that column
+                    // belongs to another launch and is skipped: the interior of a split image)
   int16_t eh;       // valid pixel rows of its last block row
   int16_t nch;      // 1: planar plane; 3, 4: interleaved channels
   int16_t bx0;      // first block column within the image

@@ -20,6 +20,12 @@ enum Kind {
   K_RT_SSE = 6,   // src -> round trip -> squared error against src per plane (nothing stored)
 };
 
+// Edge class of a launch (the codec kernel's EDGE parameter): images whose
+// sides are multiples of 8; images with edge blocks (right or bottom edge);
+// the interiors of split edge images, whose flat rows include a masked last
+// block column (descriptor ew = 0) so that their tiles stay aligned.
+enum EdgeClass { kEdgeNone = 0, kEdgeBlocks = 1, kEdgeMasked = 2 };
+
 struct LaunchShape {
   int threads;      // per CTA, multiple of 32, at most 256
   int ctas_per_sm;  // persistent grid = SMs x ctas_per_sm (at most)
@@ -37,7 +43,7 @@ struct CodecLaunch {
   unsigned long long* sse;  // K_RT_SSE: per-plane sums of squared reconstruction error (device)
   unsigned int* fault;      // checked builds: bits set by the kernels' bounds checks (device; may be NULL)
   int nch;                  // 1: planar planes; 3 or 4: interleaved images
-  bool edge;                // some image has a side that is not a multiple of 8
+  int edge;                 // edge class: 0 none, 1 edge blocks, 2 interiors with a masked last column
   QuantParams qp;
 };
 
@@ -61,6 +67,11 @@ KernelFn pick_interleaved_kernel(int kind, int qmode, bool evenq, int nch);
 KernelFn pick_interleaved_edge_kernel(int kind, int qmode, bool evenq, int nch);
 // Kernels for planar images with edge blocks (adct_codec_edge.cu).
 KernelFn pick_edge_kernel(int kind, int qmode, bool evenq);
+// Kernels for the interiors of split edge images, whose descriptors mask
+// their last block column (adct_codec_masked.cu: planar;
+// adct_codec_interleaved_masked.cu: nch = 3 or 4).
+KernelFn pick_masked_kernel(int kind, int qmode, bool evenq);
+KernelFn pick_interleaved_masked_kernel(int kind, int qmode, bool evenq, int nch);
 
 // Device allocation of the library (cudaMalloc), with failure injection for
 // tests: the environment variable ADCT_FAULT_INJECT=alloc:K makes the K-th
