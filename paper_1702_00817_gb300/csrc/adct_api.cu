@@ -131,7 +131,9 @@ struct TimedLaunch {
   adct_context* ctx;
   cudaStream_t stream;
   cudaEvent_t stop = nullptr;
-  TimedLaunch(adct_context* c, cudaStream_t s) : ctx(c), stream(s) {
+  // timed = false (under stream capture): neither counted nor timed
+  TimedLaunch(adct_context* c, cudaStream_t s, bool timed = true) : ctx(c), stream(s) {
+    if (!timed) return;
     ++ctx->launches;
     if (!ctx->timing) return;
     if (ctx->tev_used == ctx->tev.size()) {
@@ -518,27 +520,47 @@ int need_for_kind(int kind) {
   }
 }
 
-// One launch per non-empty group of t, whose tables are at dev (t.blob's layout).
-// Under stream capture (timed = false) no timing events are recorded.
-// Launches every non-empty group of a call, one after the other on `stream`.
+// Launch order of the groups: per layout class the group without edge
+// blocks, the masked interiors of its split images, then its edge group,
+// which runs as the programmatic dependent of the masked interiors when
+// there are any (its CTAs start in their tail instead of after them).
+constexpr int kLaunchOrder[kGroupsAll] = {0, 6, 1, 2, 7, 3, 4, 8, 5};
+
+// One launch per non-empty group of t, whose tables are at dev (t.blob's
+// layout), in kLaunchOrder on `stream`.  Under stream capture (timed = false)
+// no timing events are recorded; a masked-interior launch and the edge
+// launch that depends on it are timed as one.
 adct_status launch_groups(adct_context* ctx, CodecLaunch cl, const Tables& t, const char* dev, const LaunchShape& shape,
                           cudaStream_t stream, bool timed = true) {
-  for (int g = 0; g < kGroupsAll; ++g) {
+  auto group = [&](int g) {
+    CodecLaunch c = cl;
+    c.planes = (const PlaneDesc*)(dev + t.off_planes[g]);
+    c.starts = (const int64_t*)(dev + t.off_starts[g]);
+    c.nplanes = (int32_t)t.planes[g].size();
+    c.total = t.total(g);
+    c.nch = kGroupNch[g];
+    c.edge = kGroupClass[g];
+    c.after_interior = false;
+    return c;
+  };
+  for (int k = 0; k < kGroupsAll; ++k) {
+    const int g = kLaunchOrder[k];
     if (t.total(g) == 0) continue;
-    cl.planes = (const PlaneDesc*)(dev + t.off_planes[g]);
-    cl.starts = (const int64_t*)(dev + t.off_starts[g]);
-    cl.nplanes = (int32_t)t.planes[g].size();
-    cl.total = t.total(g);
-    cl.nch = kGroupNch[g];
-    cl.edge = kGroupClass[g];
+    const int ge = (kGroupClass[g] == kEdgeMasked && k + 1 < kGroupsAll) ? kLaunchOrder[k + 1] : -1;
+    const bool pair = ge >= 0 && t.total(ge) > 0;
     cudaError_t e;
-    if (timed) {
-      TimedLaunch tl(ctx, stream);
-      e = launch_codec(cl, shape, ctx->sm_count, stream);
+    {
+      TimedLaunch tl(ctx, stream, timed);
+      e = launch_codec(group(g), shape, ctx->sm_count, stream);
+      if (e == cudaSuccess && pair) {
+        if (timed) ++ctx->launches;  // two kernels
+        CodecLaunch c = group(ge);
+        c.after_interior = true;
+        e = launch_codec(c, shape, ctx->sm_count, stream);
+      }
       tl.done();
-    } else {
-      e = launch_codec(cl, shape, ctx->sm_count, stream);
     }
+    if (pair) ++k;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "codec kernel launch");
   }
   return ADCT_OK;

@@ -185,6 +185,21 @@ cudaError_t fire(const CodecLaunch& c, const Prepared& p, int grid, cudaStream_t
   const int64_t warps = (int64_t)grid * (p.threads / 32);
   int64_t chunk = (c.total + warps - 1) / warps;
   chunk = (chunk + kTile - 1) / kTile * kTile;
+  if (c.edge == kEdgeBlocks && c.after_interior) {
+    // programmatic dependent of the masked-interior launch just before it
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(p.threads);
+    cfg.dynamicSmemBytes = p.smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, p.fn, c.planes, c.starts, c.nplanes, c.total, chunk, p.stage, c.sse, c.fault,
+                              c.qp);
+  }
   p.fn<<<grid, p.threads, p.smem, stream>>>(c.planes, c.starts, c.nplanes, c.total, chunk, p.stage, c.sse, c.fault,
                                             c.qp);
   return cudaGetLastError();

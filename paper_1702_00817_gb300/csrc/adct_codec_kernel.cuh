@@ -749,7 +749,18 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
 
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t begin = gwarp * chunk;
-  if (begin >= total) return;  // whole warp exits together
+  // Programmatic dependent launch.  The interiors of split images (MASKED)
+  // let the launch of their images' edge strips, which follows them with the
+  // programmatic serialisation attribute, start at once: its CTAs take SM
+  // slots as this grid's CTAs retire.  The edge kernel (EB) waits for the
+  // grid before it, if any, before it exits, so that its completion still
+  // implies that grid's (later work on the stream sees both done); launched
+  // without the attribute it has nothing to wait for.
+  if (MASKED) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  if (begin >= total) {  // whole warp exits together
+    if (EB) asm volatile("griddepcontrol.wait;" ::: "memory");
+    return;
+  }
   const int64_t end = min(total, begin + chunk);
   const int32_t rend = (int32_t)(end - begin);  // chunk length (< 2^31 blocks)
 
@@ -941,6 +952,7 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
   }
   if (KT::sse) flush();
   cp_async_wait<0>();
+  if (EB) asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // The kernels of one zone ZS for the zonal kinds that have them; nullptr otherwise.

@@ -44,6 +44,8 @@ struct CodecLaunch {
   unsigned int* fault;      // checked builds: bits set by the kernels' bounds checks (device; may be NULL)
   int nch;                  // 1: planar planes; 3 or 4: interleaved images
   int edge;                 // edge class: 0 none, 1 edge blocks, 2 interiors with a masked last column
+  bool after_interior;      // edge class 1 right after a masked-interior launch on the same stream:
+                            // launched as its programmatic dependent (overlaps its tail)
   QuantParams qp;
 };
 

@@ -242,6 +242,32 @@ def test_graph_and_noalloc_with_layouts(codec):
         assert np.array_equal(c.cpu().numpy().astype(np.int64), qref)
 
 
+def test_graph_with_split_edge_images(codec):
+    """Images large enough to be split (a masked interior, then their edge
+    strips launched as its programmatic dependent), captured in a CUDA graph
+    and replayed, planar and interleaved in one call: equal to the oracle."""
+    q = _quant(ADCT_Q_STEP, 4, 64)
+    imgs = [(inputs.synth_image(75, 93, 31, channels=2), False),
+            (np.moveaxis(inputs.synth_image(100, 61, 32, channels=3), 0, -1).copy(), True),
+            (inputs.synth_image(72, 93, 33, channels=1), False)]
+    refs = [[_ref(np.ascontiguousarray(p), ADCT_Q_STEP, 4, 64) for p in _planes(x, inter)] for x, inter in imgs]
+    for _ in range(3):  # capture, then replay twice
+        ims = []
+        for x, inter in imgs:
+            src, _ = _pitched(x, inter)
+            dst, _ = _pitched(np.zeros_like(x), inter)
+            C = x.shape[2] if inter else x.shape[0]
+            H, W = (x.shape[0], x.shape[1]) if inter else (x.shape[1], x.shape[2])
+            ims.append(Image(src, dst, _coef(C, H, W, ADCT_Q_STEP, 64), inter))
+        codec.roundtrip_graph(ims, q)
+        torch.cuda.synchronize()
+        for im, ref, (x, inter) in zip(ims, refs, imgs):
+            for k, (qref, rec) in enumerate(ref):
+                assert np.array_equal(im.coef[k].cpu().numpy().astype(np.int64), qref)
+                out = im.dst[:, :, k] if inter else im.dst[k]
+                assert np.array_equal(out.cpu().numpy(), rec)
+
+
 def test_layout_errors(codec):
     q = _quant(ADCT_Q_STEP, 4, 64)
     two = torch.zeros((16, 16, 2), dtype=torch.uint8, device=DEV)
