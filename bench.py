@@ -613,15 +613,18 @@ def run_layout(args):
         for i in range(max(3, args.warmup)):
             step(i)
         torch.cuda.synchronize()
+        d.barrier()
+        # the call's own time: CUDA events around the steps, with no events
+        # between the calls (a call with edge images launches its interior and
+        # then its edge strips, which overlap the interior's tail)
+        t = d.max(_event_time(step, steps, stream))
+        # then the same steps again with an event pair around every launch, for
+        # the summed kernel durations reported beside it
         codec.kernel_time()
         codec.kernel_timing(True)
-        d.barrier()
-        t = d.max(_event_time(step, steps, stream))
+        _event_time(step, steps, stream)
         codec.kernel_timing(False)
         kms, launches = codec.kernel_time()
-        # a call with edge images launches its interior and its edge strips (on
-        # two streams, overlapping): the call's own time, CUDA events around the
-        # steps, is the one that counts; the summed kernel durations beside it
         cs = t / steps
         rows[name] = {"blocks_s": d.sum(blocks * steps) / t, "call_us": 1e6 * cs, "kernel_us_sum": 1e3 * kms / steps,
                       "launches_per_call": launches / steps,

@@ -30,7 +30,11 @@
 namespace adct {
 namespace {
 
-constexpr int kFloatThreads = 128;
+// One warp per CTA, 12 CTAs per SM (registers allow 12 warps): measured on
+// 64 x 3 x 512x512, the forward + adjoint pair runs in 168.7 us against
+// 174.5 us with CTAs of 4 warps, 3 per SM (the forward 69 us against 75 us).
+constexpr int kFloatThreads = 32;
+constexpr int kFloatMinCtas = 384 / kFloatThreads;  // 12 warps per SM
 
 // d_i = 2^(-a_i / 2): 1/sqrt8, 1/sqrt2, 1/2 (Sec. 2, matrix D)
 __host__ __device__ constexpr float d_of(int i) {
@@ -189,7 +193,7 @@ __device__ __forceinline__ void store_block(float* __restrict__ p, int32_t W, co
 // 16-byte halves 32 bytes apart (measured: 77.9 us -> 74.2 us for
 // 64 x 3 x 512x512).
 template <bool SOFT>
-__global__ void __launch_bounds__(kFloatThreads, 3) k_float_fwd(const float* __restrict__ x, float* __restrict__ y,
+__global__ void __launch_bounds__(kFloatThreads, kFloatMinCtas) k_float_fwd(const float* __restrict__ x, float* __restrict__ y,
                                                              const FloatShape s, const FloatParams fp) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int lane = threadIdx.x & 31;
@@ -249,7 +253,7 @@ __global__ void __launch_bounds__(kFloatThreads, 3) k_float_fwd(const float* __r
 // x_{n+1}, gy_{n+1}, so "all but the newest group done" first means x_n is
 // in, then (after x_{n+1} was committed) that gy_n is in.
 template <bool SOFT>
-__global__ void __launch_bounds__(kFloatThreads, 3) k_float_bwd(const float* __restrict__ x, const float* __restrict__ gy,
+__global__ void __launch_bounds__(kFloatThreads, kFloatMinCtas) k_float_bwd(const float* __restrict__ x, const float* __restrict__ gy,
                                                              float* __restrict__ gx, const FloatShape s,
                                                              const FloatParams fp) {
   extern __shared__ __align__(128) uint8_t smem[];
