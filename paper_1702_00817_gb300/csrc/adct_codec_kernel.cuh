@@ -390,6 +390,13 @@ __device__ __forceinline__ void read_interleaved(const uint8_t* __restrict__ in,
   }
 }
 
+// Reconstructed planar tile of one channel in lane-major order (the
+// per-channel interleaved pipeline): lane l's rows 2k and 2k + 1 form the
+// 16-byte chunk at l * 64 + ((k ^ ((l >> 1) & 3)) << 4), so that the 8 lanes
+// of each quarter warp store or load one chunk each in 8 distinct 16-byte
+// bank groups.
+__device__ __forceinline__ int recon_chunk(int lane, int k) { return lane * 64 + ((k ^ ((lane >> 1) & 3)) << 4); }
+
 // Arithmetic of one 8x8 block: read its input from the input stage, quantise,
 // stage or store q, dequantise, invert and store the pixels.
 //
@@ -580,11 +587,25 @@ __device__ __forceinline__ uint32_t block_step(int32_t (&v)[64], uint8_t* __rest
       // interleaved: the reconstructed rows back into this channel's planar
       // tile (its input is consumed), interleaved and stored once every
       // channel is done
-      uint2* pl = (uint2*)((PRE ? recon : in) + ch * 2048);
+      if (PRE) {
+        // lane-major tile (recon_chunk): rows 2k and 2k + 1 in one 16-byte store
+        uint8_t* pl = recon + ch * 2048;
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
-        pl[i * 32 + lane] = make_uint2(pixels4(v[8 * i + 0], v[8 * i + 1], v[8 * i + 2], v[8 * i + 3]),
-                                       pixels4(v[8 * i + 4], v[8 * i + 5], v[8 * i + 6], v[8 * i + 7]));
+        for (int k = 0; k < 4; ++k) {
+          const int i = 2 * k;
+          *(uint4*)(pl + recon_chunk(lane, k)) =
+              make_uint4(pixels4(v[8 * i + 0], v[8 * i + 1], v[8 * i + 2], v[8 * i + 3]),
+                         pixels4(v[8 * i + 4], v[8 * i + 5], v[8 * i + 6], v[8 * i + 7]),
+                         pixels4(v[8 * i + 8], v[8 * i + 9], v[8 * i + 10], v[8 * i + 11]),
+                         pixels4(v[8 * i + 12], v[8 * i + 13], v[8 * i + 14], v[8 * i + 15]));
+        }
+      } else {
+        uint2* pl = (uint2*)(in + ch * 2048);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          pl[i * 32 + lane] = make_uint2(pixels4(v[8 * i + 0], v[8 * i + 1], v[8 * i + 2], v[8 * i + 3]),
+                                         pixels4(v[8 * i + 4], v[8 * i + 5], v[8 * i + 6], v[8 * i + 7]));
+      }
     }
   }
   return err;
@@ -595,8 +616,9 @@ __device__ __forceinline__ uint32_t block_step(int32_t (&v)[64], uint8_t* __rest
 // (byte b of the span is byte (b / NCH) & 3 of channel b % NCH's word
 // (b / NCH) / 4) and written with NCH 8-byte stores, so the warp covers 256 NCH
 // contiguous bytes per row; on the image's right edge only the valid bytes
-// of each 8-byte part (store_prefix8).
-template <int NCH, bool EDGE>
+// of each 8-byte part (store_prefix8).  LM: the planar tiles are in the
+// lane-major order of recon_chunk and are read two rows per 16-byte load.
+template <int NCH, bool EDGE, bool LM = false>
 __device__ __forceinline__ void write_pixels_interleaved(const uint8_t* __restrict__ stage,
                                                         const PlaneDesc* __restrict__ planes, const Pos& pos,
                                                         int lane) {
@@ -605,15 +627,22 @@ __device__ __forceinline__ void write_pixels_interleaved(const uint8_t* __restri
   const int64_t pitch = __ldg(&d->pitch);
   uint8_t* o = dst_of(d) + (int64_t)(8 * pos.by) * pitch + 8 * NCH * pos.bx;
   const int vc = EDGE ? valid_cols(d, pos) : 8, vr = EDGE ? valid_rows(d, pos) : 8;
+  uint4 pair[NCH];  // LM: channel c's rows 2k and 2k + 1
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     if (i >= vr) break;
     uint32_t q[2 * NCH];  // channel c's pixels 0-3 and 4-7 at q[2c], q[2c + 1]
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
-      const uint2 u = ((const uint2*)(stage + c * 2048))[i * 32 + lane];
-      q[2 * c] = u.x;
-      q[2 * c + 1] = u.y;
+      if (LM) {
+        if ((i & 1) == 0) pair[c] = *(const uint4*)(stage + c * 2048 + recon_chunk(lane, i >> 1));
+        q[2 * c] = (i & 1) ? pair[c].z : pair[c].x;
+        q[2 * c + 1] = (i & 1) ? pair[c].w : pair[c].y;
+      } else {
+        const uint2 u = ((const uint2*)(stage + c * 2048))[i * 32 + lane];
+        q[2 * c] = u.x;
+        q[2 * c + 1] = u.y;
+      }
     }
     uint32_t span[2 * NCH];
 #pragma unroll
@@ -944,7 +973,7 @@ k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts
 #pragma unroll 1
       for (int ch = 0; ch < NCH; ++ch) channel(ch);
     }
-    if (NCH > 1 && KT::inv && !KT::sse) write_pixels_interleaved<NCH, EB>(recon, planes, pc, lane);
+    if (NCH > 1 && KT::inv && !KT::sse) write_pixels_interleaved<NCH, EB, kLazy>(recon, planes, pc, lane);
 #pragma unroll
     for (int k = 0; k + 1 < S - 1; ++k) ring[k] = ring[k + 1];
     ring[S - 2] = pl;
