@@ -752,8 +752,15 @@ __device__ __forceinline__ void write_back_zz(const uint8_t* __restrict__ stage_
   }
 }
 
+// Three CTAs of 4 warps per SM (up to 168 registers), four for the packed
+// zonal kernels of zones 6-8 (128 registers, no spills): r = 25 on 256 x
+// 1080x1920 takes 275.6 us against 298 us at 158 registers and 3 CTAs per
+// SM; zone 5 (113 registers) and the others are unchanged or slower at 128.
+template <int QMODE, int ZS>
+constexpr int codec_min_ctas() { return (QMODE == QM_ZONAL_ZZ && ZS >= 6 && ZS <= 8) ? 4 : 3; }
+
 template <int KIND, int QMODE, bool EVENQ, int ZS, int NCH = 1, int EDGE = kEdgeNone>
-__global__ void __launch_bounds__(kMaxThreads, 3)
+__global__ void __launch_bounds__(kMaxThreads, codec_min_ctas<QMODE, ZS>())
 k_codec(const PlaneDesc* __restrict__ planes, const int64_t* __restrict__ starts, int32_t nplanes, int64_t total,
         int64_t chunk, int stage_coef, unsigned long long* __restrict__ sse, unsigned int* __restrict__ fault,
         const QuantParams qp) {
