@@ -15,7 +15,9 @@
 // because a thread moves its block from shared memory into registers before
 // the next copy into that stage is issued.  The forward also stages its
 // output tile, so that its stores are 512-byte warp writes too; the adjoint
-// stores directly (its stages hold x and gy, and a third would cost warps).
+// stages its output in the gy tile once that has been read, and issues the
+// next gy copy after the write-back (a third tile would cost warps; measured:
+// 104.5 us -> 100.3 us against direct stores, 64 x 3 x 512x512).
 //
 // Soft quantiser phase: sin and cos of 2 pi h, h = y / Q, by range reduction
 // (h minus the nearest integer, then the symmetries sin(2 pi b) = sin(2 pi
@@ -178,14 +180,6 @@ __device__ __forceinline__ void read_block(const uint8_t* tile, int lane, float*
     }
 }
 
-__device__ __forceinline__ void store_block(float* __restrict__ p, int32_t W, const float* v) {
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    __stcs((float4*)(p + (int64_t)i * W), make_float4(v[8 * i + 0], v[8 * i + 1], v[8 * i + 2], v[8 * i + 3]));
-    __stcs((float4*)(p + (int64_t)i * W) + 1, make_float4(v[8 * i + 4], v[8 * i + 5], v[8 * i + 6], v[8 * i + 7]));
-  }
-}
-
 // Forward: each warp walks tiles g0, g0 + step, ... (step = all threads of
 // the grid), copying tile n + 1 while computing tile n.  The results go
 // through a second tile in shared memory (same layout), from which the warp
@@ -248,8 +242,9 @@ __global__ void __launch_bounds__(kFloatThreads, kFloatMinCtas) k_float_fwd(cons
 }
 
 // Adjoint.  SOFT: the x tile n + 1 is copied while tile n's y and
-// d_i d_j (1 - cos(2 pi y / Q)) are computed, and the gy tile n + 1 while
-// tile n is inverted and stored.  Copy groups are committed in the order
+// d_i d_j (1 - cos(2pi y / Q)) are computed, and the gy tile n + 1 (issued
+// once tile n's gx has been staged in the gy tile and written back) while
+// tile n + 1's y is recomputed.  Copy groups are committed in the order
 // x_{n+1}, gy_{n+1}, so "all but the newest group done" first means x_n is
 // in, then (after x_{n+1} was committed) that gy_n is in.
 template <bool SOFT>
@@ -309,12 +304,32 @@ __global__ void __launch_bounds__(kFloatThreads, kFloatMinCtas) k_float_bwd(cons
           v[k] = SOFT ? r[e] * v[k] : r[e] * (d_of(i) * d_of(j));
         }
       }
+    // the gy tile has been read: stage this tile's gx in it and write it back
+    // with 512-byte warp stores, then refill it with the next gy tile
+    __syncwarp();
+    if (cur >= 0) {
+      inv2d(v);
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+          *(float4*)(tg + (i * 64 + swz(2 * lane + c)) * 16) =
+              make_float4(v[8 * i + 4 * c], v[8 * i + 4 * c + 1], v[8 * i + 4 * c + 2], v[8 * i + 4 * c + 3]);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int q = 32 * k + lane;
+      const int64_t o = __shfl_sync(0xffffffffu, cur, q >> 1);
+      if (o >= 0) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          __stcs((float4*)(gx + o + 4 * (q & 1) + (int64_t)i * s.W), *(const float4*)(tg + (i * 64 + swz(q)) * 16));
+      }
+    }
     __syncwarp();
     issue_tile(tg, gy, off, s, lane);
     cp_async_commit();
-    if (cur < 0) continue;
-    inv2d(v);
-    store_block(gx + cur, s.W, v);
   }
   cp_async_wait<0>();
 }
